@@ -1,0 +1,194 @@
+"""Discrete heat operator and one-slice propagators, FP64, plain numpy.
+
+Problem (§3.1, Eq. (8)-(9)): u_t = div(kappa grad u) on the unit interval,
+square or cube, zero Dirichlet boundary (h(u,s,t) = 0 on the boundary).
+Space: uniform grid, interior sizes n per axis, h_a = 1/(n_a+1), finite
+volumes in flux form
+
+    (A u)_p = sum_axes h_a^-2 sum_{faces f=(p,q)} kappa_f (u_p - u_q),
+    kappa_f = (kappa_p + kappa_q) / 2,   u_q = 0 outside the grid,
+
+with kappa given at every node including the boundary ring (kappa = None
+means kappa = 1, the standard 3/5/7-point negative Laplacian).
+
+One slice [T_{i-1}, T_i] is propagated by (§3.1, definitions of F and G;
+§5.1, backward Euler and the time steps dT, dt):
+  * explicit Euler:  u <- u - dt A u              (fine, n_f steps)
+  * implicit Euler:  (I + dt A) u_new = u         (fine in 1D, coarse always)
+    solved by the Thomas algorithm (1D, exact) or by conjugate gradients
+    (2D/3D) stopped when ||r||_2 <= rtol ||b||_2.
+
+Arrays use the layout of ``synthetic.generators``: interior states have
+numpy shape (nx,), (ny, nx) or (nz, ny, nx); kappa has n+2 per axis.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def _h_of_axis(h, ndim: int, ax: int) -> float:
+    # numpy axis 0 is the slowest grid axis (z in 3D, y in 2D); h is (hx, hy, hz)
+    return h[ndim - 1 - ax]
+
+
+def apply_A(u: np.ndarray, h, kappa: np.ndarray | None = None) -> np.ndarray:
+    """A_kappa u in flux form (definition above), zero Dirichlet boundary."""
+    d = u.ndim
+    U = np.pad(u, 1)  # zero boundary ring
+    out = np.zeros_like(u)
+    for ax in range(d):
+        # restrict every other axis to interior indices
+        inner = [slice(1, -1)] * d
+        inner[ax] = slice(None)
+        Ua = U[tuple(inner)]
+        hi = [slice(None)] * d
+        lo = [slice(None)] * d
+        hi[ax] = slice(1, None)
+        lo[ax] = slice(None, -1)
+        diff = Ua[tuple(hi)] - Ua[tuple(lo)]        # u_{j+1} - u_j on the n+1 faces
+        if kappa is None:
+            kf = 1.0
+        else:
+            Ka = kappa[tuple(inner)]
+            kf = 0.5 * (Ka[tuple(hi)] + Ka[tuple(lo)])  # face diffusivity
+        flux = kf * diff
+        # -(flux_{p+1/2} - flux_{p-1/2}) / h^2 at the interior nodes
+        out -= (flux[tuple(hi)] - flux[tuple(lo)]) / _h_of_axis(h, d, ax) ** 2
+    return out
+
+
+def explicit_euler(u: np.ndarray, dt: float, h, kappa=None, steps: int = 1) -> np.ndarray:
+    """`steps` explicit Euler steps u <- u - dt A u (fine propagator F, §5.1)."""
+    u = np.array(u, dtype=np.float64, copy=True)
+    for _ in range(steps):
+        u = u - dt * apply_A(u, h, kappa)
+    return u
+
+
+def tridiagonal_1d(n: int, dt: float, h, kappa=None):
+    """Bands (sub, diag, sup) of I + dt A in 1D (length n each; sub[0], sup[-1] unused)."""
+    hx = h[0]
+    if kappa is None:
+        kf = np.ones(n + 1)
+    else:
+        kf = 0.5 * (kappa[1:] + kappa[:-1])          # n+1 faces
+    r = dt / hx ** 2
+    diag = 1.0 + r * (kf[:-1] + kf[1:])
+    sub = np.zeros(n)
+    sup = np.zeros(n)
+    sub[1:] = -r * kf[1:-1]
+    sup[:-1] = -r * kf[1:-1]
+    return sub, diag, sup
+
+
+def thomas(sub, diag, sup, rhs: np.ndarray) -> np.ndarray:
+    """Thomas algorithm (Gaussian elimination without pivoting) on the last axis.
+
+    rhs may carry leading batch axes; the bands are shared by the batch.
+    """
+    n = diag.shape[0]
+    rhs = np.array(rhs, dtype=np.float64, copy=True)
+    c = np.zeros(n)
+    d = np.zeros_like(rhs)
+    c[0] = sup[0] / diag[0]
+    d[..., 0] = rhs[..., 0] / diag[0]
+    for m in range(1, n):
+        denom = diag[m] - sub[m] * c[m - 1]
+        c[m] = sup[m] / denom
+        d[..., m] = (rhs[..., m] - sub[m] * d[..., m - 1]) / denom
+    x = np.zeros_like(rhs)
+    x[..., n - 1] = d[..., n - 1]
+    for m in range(n - 2, -1, -1):
+        x[..., m] = d[..., m] - c[m] * x[..., m + 1]
+    return x
+
+
+def implicit_euler_1d(u: np.ndarray, dt: float, h, kappa=None, steps: int = 1) -> np.ndarray:
+    """`steps` backward-Euler steps in 1D by the Thomas algorithm (§5.1, LU solve)."""
+    n = u.shape[-1]
+    sub, diag, sup = tridiagonal_1d(n, dt, h, kappa)
+    x = np.array(u, dtype=np.float64, copy=True)
+    for _ in range(steps):
+        x = thomas(sub, diag, sup, x)
+    return x
+
+
+def cg_implicit_euler(b: np.ndarray, dt: float, h, kappa=None, x0=None,
+                      rtol: float = 1e-10, maxit: int = 10000):
+    """One backward-Euler step (I + dt A) x = b by textbook conjugate gradients.
+
+    Hestenes-Stiefel CG from x0 (x0 = b when None); stops as soon as the
+    recursively updated residual satisfies ||r||_2 <= rtol ||b||_2, when the
+    residual is exactly zero, or after maxit iterations.  Returns (x, iters).
+    """
+    b = np.asarray(b, dtype=np.float64)
+    x = np.array(b if x0 is None else x0, dtype=np.float64, copy=True)
+
+    def op(v):
+        return v + dt * apply_A(v, h, kappa)
+
+    bnorm = np.sqrt(np.sum(b * b))
+    r = b - op(x)
+    rr = np.sum(r * r)
+    it = 0
+    if np.sqrt(rr) <= rtol * bnorm or rr == 0.0:
+        return x, it
+    p = r.copy()
+    while it < maxit:
+        q = op(p)
+        alpha = rr / np.sum(p * q)
+        x = x + alpha * p
+        r = r - alpha * q
+        rr_new = np.sum(r * r)
+        it += 1
+        if np.sqrt(rr_new) <= rtol * bnorm or rr_new == 0.0:
+            break
+        beta = rr_new / rr
+        p = r + beta * p
+        rr = rr_new
+    return x, it
+
+
+class Propagators:
+    """F and G of one problem (§3.1): F accurate, G cheap, both over one slice.
+
+    prob keys: dim, n, h, dt (fine step), f_steps, f_scheme ('explicit' or
+    'implicit'), g_solver ('thomas' or 'cg'), g_steps (default 1), g_rtol,
+    g_maxit, kappa.  The coarse step is dT = f_steps * dt.
+    """
+
+    def __init__(self, prob: dict, kappa="from_prob"):
+        self.dim = prob["dim"]
+        self.n = tuple(prob["n"])
+        self.h = tuple(prob["h"])
+        self.dt = float(prob["dt"])
+        self.f_steps = int(prob["f_steps"])
+        self.f_scheme = prob.get("f_scheme", "explicit")
+        self.g_solver = prob.get("g_solver", "cg" if self.dim > 1 else "thomas")
+        self.g_steps = int(prob.get("g_steps", 1))
+        self.g_rtol = float(prob.get("g_rtol", 1e-10))
+        self.g_maxit = int(prob.get("g_maxit", 20000))
+        self.kappa = prob.get("kappa") if isinstance(kappa, str) else kappa
+        self.dT = self.f_steps * self.dt
+        self.shape = tuple(reversed(self.n))
+        if self.g_solver == "cg" and self.g_steps != 1:
+            raise ValueError("CG coarse propagator takes one implicit step")
+
+    def F(self, x: np.ndarray) -> np.ndarray:
+        x = np.asarray(x, dtype=np.float64).reshape(self.shape)
+        if self.f_scheme == "explicit":
+            return explicit_euler(x, self.dt, self.h, self.kappa, self.f_steps)
+        if self.dim != 1:
+            raise ValueError("implicit fine propagator is 1D (Thomas) only")
+        return implicit_euler_1d(x, self.dt, self.h, self.kappa, self.f_steps)
+
+    def G(self, x: np.ndarray, x0=None):
+        """Returns (G(x), cg_iterations); x0 is the CG starting guess."""
+        x = np.asarray(x, dtype=np.float64).reshape(self.shape)
+        dTg = self.dT / self.g_steps
+        if self.g_solver == "thomas":
+            if self.dim != 1:
+                raise ValueError("Thomas coarse propagator is 1D only")
+            return implicit_euler_1d(x, dTg, self.h, self.kappa, self.g_steps), 0
+        x0 = None if x0 is None else np.asarray(x0, dtype=np.float64).reshape(self.shape)
+        return cg_implicit_euler(x, dTg, self.h, self.kappa, x0, self.g_rtol, self.g_maxit)
