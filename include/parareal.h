@@ -1,0 +1,197 @@
+/*
+ * parareal.h — C ABI of the GB300 (sm_103a) Parareal library for the heat
+ * equation u_t = div(kappa grad u) with zero Dirichlet boundary.
+ *
+ * Method: Parareal (§3.1, Eq. (11)) run as Algorithm 1 (§4.1), and
+ * asynchronous Parareal (§3.1, Eq. (12)) run as Algorithm 2 (§4.1), with
+ * the stopping test of §5.1, Eq. (22).  The problem statement follows §3.1
+ * (Eq. (8)-(10)): a time interval [T0, T] cut into N slices, initial values
+ * u0, zero Dirichlet boundary, a fine propagator F and a coarse propagator G
+ * over one slice, and a tolerance on the max-norm increment.
+ *
+ * Conventions shared by every entry point
+ *  - Grid: dim = 1, 2 or 3; n[a] interior points per axis a (x, y, z);
+ *    h_a = 1/(n[a]+1) on the unit interval/square/cube.  A state holds
+ *    M = n[0]*n[1]*n[2] doubles (unused n[a] = 1), x fastest, then y, then z.
+ *  - Trajectory lam: (N+1) states, row i = state at T_i (row 0 = u0),
+ *    contiguous, (N+1)*M doubles, slice index slowest.
+ *  - kappa: diffusivity at every node including the boundary ring,
+ *    prod(n[a]+2) doubles in the same x-fastest order, or NULL for kappa = 1.
+ *    Face values are the mean of the two node values (flux form).
+ *  - Pointers named *_dev are device pointers (cudaMalloc / torch CUDA
+ *    tensors); *_host are host pointers.  The caller owns every buffer it
+ *    passes; the library owns only its context and workspaces.
+ *  - Alignment: device arrays must be 16-byte aligned (vector loads).
+ *  - Work is issued on the stream given to parareal_create; calls that
+ *    return results or statistics synchronise that stream before returning.
+ *  - Every function returns PR_OK (0) or a PR_E* code and never throws;
+ *    parareal_last_error gives a one-line message for the last failure.
+ */
+#ifndef PARAREAL_H
+#define PARAREAL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pr_ctx pr_ctx; /* opaque; owns workspaces only */
+
+enum pr_status {
+  PR_OK = 0,
+  PR_EINVAL = 1,    /* invalid argument or problem (sizes, alignment, stability) */
+  PR_ENOMEM = 2,    /* device allocation failed */
+  PR_ECUDA = 3,     /* a CUDA call failed */
+  PR_ETIMEOUT = 4,  /* an asynchronous run exceeded its wall-clock limit */
+  PR_ENOTCONV = 5,  /* max_iter reached before the tolerance; results written */
+  PR_ESTATE = 6,    /* call out of order (e.g. run before set_problem) */
+  PR_ELOGFULL = 7   /* asynchronous event log capacity exceeded; run stopped */
+};
+
+enum pr_scheme { PR_EXPLICIT_EULER = 0, PR_IMPLICIT_EULER = 1 };
+enum pr_solver { PR_SOLVER_THOMAS = 0, PR_SOLVER_CG = 1 };
+
+/* Problem statement (§3.1).  Scalars are copied by parareal_set_problem;
+ * u0_dev and kappa_dev are borrowed and must stay valid while the context
+ * uses this problem.
+ *  f_scheme/f_steps: F = f_steps steps of explicit Euler (any dim) or
+ *    implicit Euler (dim 1, Thomas) of size dt = (T-T0)/(N*f_steps).
+ *  f_prec: 64 = FP64 fine steps; 32 = FP32 fine steps with FP64 input and
+ *    output (the coarse sweep, correction and test stay FP64).
+ *  g_solver: PR_SOLVER_THOMAS (dim 1) or PR_SOLVER_CG; G = one implicit
+ *    Euler step of size dT = (T-T0)/N (g_steps must be 1 with CG).
+ *  g_rtol/g_maxit: CG stops when ||r||_2 <= g_rtol*||b||_2 or after g_maxit.
+ *  tol: stop when max_i max_x |lam_i^{k+1} - lam_i^k| < tol (Eq. (22));
+ *    tol = 0 runs exactly max_iter iterations.
+ *  max_iter: iteration cap (<= N; finite termination at k = N, §3.2). */
+typedef struct pr_problem {
+  int dim;
+  int n[3];
+  double T0, T;
+  int N;
+  const double* u0_dev;
+  const double* kappa_dev;
+  int f_scheme;
+  int f_steps;
+  int f_prec;
+  int g_solver;
+  int g_steps;
+  double g_rtol;
+  int g_maxit;
+  double tol;
+  int max_iter;
+} pr_problem;
+
+/* Run statistics. */
+typedef struct pr_stats {
+  int iterations;          /* sync: k; async: kappa(k~) = max_i k_i (§4.1) */
+  int converged;           /* 1 if the tolerance (or finite termination) stopped the run */
+  double max_delta;        /* last max_i delta_i */
+  long long fine_lups;     /* fine cell updates executed (sum over F applications) */
+  long long cg_iterations; /* CG iterations executed by all coarse solves */
+  long long coarse_solves; /* number of G applications that ran a solver */
+  double t_total_ms;       /* wall time of the run on the device (CUDA events) */
+  double t_fine_ms;        /* sync: time in batched F (events); async: 0 */
+  double t_coarse_ms;      /* sync: time in predictor + coarse sweeps; async: 0 */
+  long long events;        /* async: slice updates published */
+  long long launches;      /* CUDA kernel launches issued by the call */
+} pr_stats;
+
+/* Asynchronous run options (Algorithm 2). */
+typedef struct pr_async_opts {
+  int paper_literal;        /* 1: a slice re-iterates even when its inputs are unchanged */
+  double timeout_s;         /* wall-clock limit of the persistent kernel (e.g. 60) */
+  const int32_t* delays_dev;/* NULL, or device int32 [N * delay_cols]: publish delay of
+                               slice i's e-th update, in units of delay_unit_ns */
+  int delay_cols;           /* columns of delays_dev (events beyond it use column e % delay_cols) */
+  double delay_unit_ns;     /* duration of one delay unit */
+  int ctas_per_slice;       /* CTAs cooperating on one slice update (0 = automatic) */
+  int quiescence;           /* 1: ignore tol and run until no slice can change */
+} pr_async_opts;
+
+/* One asynchronous update event (log entry). */
+typedef struct pr_event {
+  int32_t slice;    /* i in 1..N */
+  int32_t version;  /* k_i after the update (1, 2, ...) */
+  int32_t vF;       /* version of lam_{i-1} used for F and the subtracted G (tau_{i-1,2}) */
+  int32_t vG;       /* version of lam_{i-1} used for the new G (tau_{i-1,1}) */
+  int32_t cg_iters; /* CG iterations of the new G (0 when vG == vF) */
+  int32_t team;     /* worker team that ran the update */
+  double delta;     /* max_x |lam_i^{version} - lam_i^{version-1}| */
+  uint64_t t_start; /* %globaltimer ns at update start */
+  uint64_t t_end;   /* %globaltimer ns when the new version became visible */
+} pr_event;
+
+/* Create a context on CUDA device `device`, issuing work on `cuda_stream`
+ * (a cudaStream_t; NULL = legacy default stream).  *out receives the context. */
+int parareal_create(pr_ctx** out, int device, void* cuda_stream);
+
+/* Validate and bind a problem (§3.1); allocates the workspaces it needs
+ * (about 4 N M doubles for the sync path).  Rejects an unstable explicit step
+ * (dt * bound(lambda_max(A)) > 2) with PR_EINVAL. */
+int parareal_set_problem(pr_ctx* ctx, const pr_problem* prob);
+
+/* Synchronous Parareal, Algorithm 1 (§4.1) / Eq. (11): predictor G-chain,
+ * batched F over the active slices, sequential coarse sweep with the fused
+ * correction lam_i = (w_new + v_i) - w_old and per-slice max-norm increment,
+ * stop test Eq. (22).  lam_out_dev: (N+1)*M doubles, written with the final
+ * iterate (row 0 = u0).  Returns PR_ENOTCONV if max_iter < N stopped it. */
+int parareal_run_sync(pr_ctx* ctx, double* lam_out_dev, pr_stats* stats);
+
+/* Same as parareal_run_sync with host buffers: copies u0_host (M doubles) to
+ * the device, runs, and copies the (N+1)*M result into lam_out_host.  The
+ * problem's u0_dev is ignored for this call. */
+int parareal_run_sync_host(pr_ctx* ctx, const double* u0_host, double* lam_out_host,
+                           pr_stats* stats);
+
+/* Asynchronous Parareal, Eq. (12) / Algorithm 2 (§4.1), as one persistent
+ * kernel: slice teams publish versions of lam_i through release/acquire
+ * flags and take the freshest visible predecessor version, with no global
+ * barrier.  lam_out_dev receives each slice's last published version.
+ * log_host (capacity log_cap events, may be NULL) receives the event log in
+ * publication order; *log_len its length. */
+int parareal_run_async(pr_ctx* ctx, const pr_async_opts* opts, double* lam_out_dev,
+                       pr_stats* stats, pr_event* log_host, size_t log_cap, size_t* log_len);
+
+/* Serial fine solution lam*_i = F(lam*_{i-1}) (Eq. (10)); (N+1)*M doubles. */
+int parareal_serial_fine(pr_ctx* ctx, double* lam_out_dev, pr_stats* stats);
+
+/* F applied to `count` states in_dev[c*M..] -> out_dev[c*M..] (batched over
+ * slices, §4.1 F step).  in and out must not overlap. */
+int parareal_fine(pr_ctx* ctx, const double* in_dev, double* out_dev, int count);
+
+/* G applied to one state: out = (I + dT A)^{-1} in (one implicit Euler
+ * step, §5.1).  x0_dev: CG starting guess (NULL = in).  *cg_iters (host,
+ * may be NULL) receives the CG iteration count (0 for Thomas). */
+int parareal_coarse(pr_ctx* ctx, const double* in_dev, const double* x0_dev, double* out_dev,
+                    int* cg_iters);
+
+/* The fused correction and increment of Algorithm 1 on one state:
+ * lam_new = (w_new + v) - w_old (in this operation order, no FMA), written
+ * over lam_inout_dev, whose old value gives *delta = max_x |lam_new - lam_old|. */
+int parareal_correct(pr_ctx* ctx, const double* w_new_dev, const double* v_dev,
+                     const double* w_old_dev, double* lam_inout_dev, double* delta);
+
+/* Discrete adjoint (reverse mode) of K synchronous iterations (Algorithm 1
+ * with the prefix frozen, no early stop) of the trajectory map u0 -> lam_N^K,
+ * G taken as the exact solve (I + dT A)^{-1} (CG to g_rtol).  Given
+ * dL/dlam_N (M doubles), writes grad_u0_dev (M doubles) and, if non-NULL,
+ * grad_kappa_dev (prod(n+2) doubles, one per node including the ring).
+ * Fine states are recomputed from slice-boundary checkpoints. */
+int parareal_adjoint(pr_ctx* ctx, const double* dL_dlamN_dev, int K, double* grad_u0_dev,
+                     double* grad_kappa_dev);
+
+/* Per-slice statistics of the last run (host arrays of N entries, may be NULL):
+ * k_i (async update counts; sync: k for every slice) and delta_i. */
+int parareal_slice_stats(pr_ctx* ctx, int* k_host, double* delta_host);
+
+void parareal_destroy(pr_ctx* ctx);
+const char* parareal_last_error(const pr_ctx* ctx);
+const char* parareal_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PARAREAL_H */

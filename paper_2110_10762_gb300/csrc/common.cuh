@@ -1,0 +1,155 @@
+// Internal declarations shared by the CUDA translation units of libparareal.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/parareal.h"
+
+namespace pr {
+
+// Grid geometry of one state (interior points only), x fastest.
+struct Geom {
+  int dim;
+  int nx, ny, nz;
+  long long M;      // nx*ny*nz
+  double hx, hy, hz;
+};
+
+// Coefficients of one constant-coefficient explicit step
+//   u' = c0 u + rx (W+E) + ry (S+N) + rz (B+F),  r_a = dt/h_a^2, c0 = 1 - 2 sum r_a
+// or, for variable kappa, per-face arrays (see StencilVar).
+struct StencilConst {
+  double c0, rx, ry, rz;
+};
+
+// Variable-kappa step u' = c0[p] u + sum_faces c_f u_q, with face arrays
+//   cx: (nz*ny) lines of (nx+1) faces, face xf sits between nodes xf-1 and xf
+//   cy: nz planes of (ny+1)*nx, face yf between rows yf-1 and yf
+//   cz: (nz+1)*ny*nx
+// For F: c_f = dt kappa_f / h^2 and c0 = 1 - sum of the node's faces.
+// For G (operator I + dT A): c_f = dT kappa_f / h^2 and c0 = 1 + sum (the
+// off-diagonal entries are -c_f).
+template <typename T>
+struct StencilVar {
+  const T* c0;
+  const T* cx;
+  const T* cy;
+  const T* cz;
+};
+
+// Partition-method tables for the batched 1D tridiagonal solves (one per
+// matrix: fine step and coarse step).  Built on the device by tridiag_setup.
+struct TriTables {
+  int n = 0;            // unknowns
+  int P = 0;            // chunks (lanes used), each with >= 2 rows
+  int levels = 0;       // PCR levels of the reduced system (2P rows)
+  double* buf = nullptr;  // device tables (layout in tridiag.cu)
+};
+
+}  // namespace pr
+
+struct pr_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int num_sms = 0;
+  int cg_blocks = 0;         // co-resident blocks for the cooperative CG kernel
+  bool has_problem = false;
+  pr_problem prob{};
+  pr::Geom g{};
+  double dt = 0, dT = 0;
+  bool var_kappa = false;
+  pr::StencilConst fst{}, gst{};   // constant-coefficient F step and G operator
+  // variable-kappa coefficient arrays (device)
+  double* fcoef = nullptr;   // F: c0, cx, cy, cz (FP64)
+  float* fcoef32 = nullptr;  // F: FP32 copy for the mixed form
+  double* gcoef = nullptr;   // G: c0, cx, cy, cz
+  pr::StencilVar<double> fvar{}, gvar{};
+  pr::StencilVar<float> fvar32{};
+  // 1D implicit tables
+  pr::TriTables tri_f{}, tri_g{};
+  // workspaces
+  double* v = nullptr;       // N*M fine outputs v_i (row i-1)
+  double* w = nullptr;       // N*M coarse values w_i (row i-1)
+  double* tmp = nullptr;     // N*M ping-pong for explicit F
+  float* f32a = nullptr;     // N*M FP32 ping-pong (mixed form)
+  float* f32b = nullptr;
+  double* cg_x = nullptr;    // CG vectors (M each)
+  double* cg_r = nullptr;
+  double* cg_p = nullptr;
+  double* cg_q = nullptr;
+  double* cg_part = nullptr; // per-block partial sums (2 parities x 3 values x cg_blocks)
+  int* cg_iters_dev = nullptr;   // per slot CG iteration counts (N+1)
+  unsigned long long* delta_dev = nullptr;  // per slice increments (N), bits of non-negative doubles
+  double* u0_stage = nullptr;    // host-API staging (M)
+  double* lam_stage = nullptr;   // host-API staging ((N+1)*M)
+  size_t lam_stage_bytes = 0;
+  // last-run per-slice statistics (host)
+  std::vector<int> last_k;
+  std::vector<double> last_delta;
+  cudaEvent_t ev[6] = {};
+  std::string err;
+  // async / adjoint workspaces are allocated lazily by their drivers
+  void* async_ws = nullptr;
+  size_t async_ws_bytes = 0;
+  void* adj_ws = nullptr;
+  size_t adj_ws_bytes = 0;
+};
+
+namespace pr {
+
+int fail(pr_ctx* c, int code, const std::string& msg);
+int cuda_fail(pr_ctx* c, cudaError_t e, const char* where);
+
+#define PR_CUDA(ctx, call)                                  \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return pr::cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+// ---- explicit fine propagator (stencil.cu)
+// Apply `steps` explicit Euler steps to `count` states.  in/out are FP64;
+// prec 64 computes in FP64 with the tmp ping-pong buffer, prec 32 computes
+// in FP32 through the two FP32 buffers.  Returns a cudaError_t.
+cudaError_t explicit_fine(pr_ctx* c, const double* in, double* out, int count, int steps,
+                          int prec);
+cudaError_t build_var_coefficients(pr_ctx* c);
+
+// ---- tridiagonal partition solver (tridiag.cu)
+cudaError_t tri_build(pr_ctx* c, TriTables* t, int n, double r, const double* kappa);
+void tri_free(TriTables* t);
+// Solve `steps` times (I + r A) x = b in place for `count` right-hand sides.
+cudaError_t tri_solve_steps(pr_ctx* c, const TriTables* t, const double* in, double* out,
+                            int count, int steps);
+
+// ---- CG coarse solver (cg.cu)
+// Epilogue modes of the cooperative CG kernel.
+enum CgMode { CG_PLAIN = 0, CG_PREDICTOR = 1, CG_CORRECT = 2 };
+struct CgArgs {
+  const double* b;     // right-hand side
+  const double* x0;    // start (may equal out for in-place warm start)
+  double* out;         // PLAIN: solution; PREDICTOR: w_i; CORRECT: w_i (in: w_old, out: w_new)
+  double* lam;         // PREDICTOR: lam_i = x; CORRECT: lam_i in/out
+  const double* v;     // CORRECT: fine value v_i
+  unsigned long long* delta;  // CORRECT: max |lam_new - lam_old| (double bits), zeroed by the kernel
+  int* iters;          // CG iterations (one int)
+  int mode;
+};
+cudaError_t cg_solve(pr_ctx* c, const CgArgs& a);
+int cg_max_blocks(int num_sms);
+cudaError_t correct(pr_ctx* c, const double* w_new, const double* v, const double* w_old,
+                    double* lam, unsigned long long* delta);
+// Generic dense helpers
+cudaError_t vec_copy(pr_ctx* c, double* dst, const double* src, long long n);
+
+// ---- asynchronous persistent kernel (async.cu)
+int run_async(pr_ctx* c, const pr_async_opts* o, double* lam_out, pr_stats* st, pr_event* log,
+              size_t log_cap, size_t* log_len);
+
+// ---- adjoint (adjoint.cu)
+int run_adjoint(pr_ctx* c, const double* gN, int K, double* grad_u0, double* grad_kappa);
+
+}  // namespace pr

@@ -1,0 +1,320 @@
+// Device building blocks shared by the cooperative CG kernel, the
+// asynchronous persistent kernel and the adjoint kernels: pointwise stencils,
+// fixed-order reductions, a bounded team barrier, and the CG iteration
+// written once for any group of co-resident blocks.
+#pragma once
+
+#include "common.cuh"
+
+namespace pr {
+
+// ----------------------------------------------------------------- stencils
+// Pointwise explicit-Euler step u' = c0 u + sum_faces c_f u_q at linear index idx.
+template <typename T, typename Tin>
+__device__ __forceinline__ T fstep_at(const Geom& g, T c0, T rx, T ry, T rz, bool var,
+                                      const StencilVar<T>& cv, const Tin* __restrict__ u,
+                                      long long idx) {
+  const int x = idx % g.nx;
+  const long long rest = idx / g.nx;
+  const int y = rest % g.ny;
+  const int z = rest / g.ny;
+  const long long plane = (long long)g.nx * g.ny;
+  const T w = x > 0 ? T(u[idx - 1]) : T(0);
+  const T e = x + 1 < g.nx ? T(u[idx + 1]) : T(0);
+  const T s = y > 0 ? T(u[idx - g.nx]) : T(0);
+  const T n = y + 1 < g.ny ? T(u[idx + g.nx]) : T(0);
+  const T b = z > 0 ? T(u[idx - plane]) : T(0);
+  const T f = z + 1 < g.nz ? T(u[idx + plane]) : T(0);
+  const T uc = T(u[idx]);
+  if (!var) {
+    T res = c0 * uc + rx * (w + e);
+    if (g.dim > 1) res += ry * (s + n);
+    if (g.dim > 2) res += rz * (b + f);
+    return res;
+  }
+  const long long fx = ((long long)z * g.ny + y) * (g.nx + 1) + x;
+  T res = cv.c0[idx] * uc + cv.cx[fx] * w + cv.cx[fx + 1] * e;
+  if (g.dim > 1) {
+    const long long fy = ((long long)z * (g.ny + 1) + y) * g.nx + x;
+    res += cv.cy[fy] * s + cv.cy[fy + g.nx] * n;
+  }
+  if (g.dim > 2) res += cv.cz[idx] * b + cv.cz[idx + plane] * f;
+  return res;
+}
+
+// (I + dT A) u at linear index idx; constant coefficients c0 = 1 + 2 sum R_a and
+// off-diagonals -R_a, or the variable-kappa arrays (diagonal c0, faces positive).
+__device__ __forceinline__ double gop_at(const Geom& g, const StencilConst& k, bool var,
+                                         const StencilVar<double>& gv,
+                                         const double* __restrict__ u, long long idx) {
+  const int x = idx % g.nx;
+  const long long rest = idx / g.nx;
+  const int y = rest % g.ny;
+  const int z = rest / g.ny;
+  const long long plane = (long long)g.nx * g.ny;
+  const double w = x > 0 ? u[idx - 1] : 0.0;
+  const double e = x + 1 < g.nx ? u[idx + 1] : 0.0;
+  const double s = y > 0 ? u[idx - g.nx] : 0.0;
+  const double n = y + 1 < g.ny ? u[idx + g.nx] : 0.0;
+  const double bz = z > 0 ? u[idx - plane] : 0.0;
+  const double fz = z + 1 < g.nz ? u[idx + plane] : 0.0;
+  const double uc = u[idx];
+  if (!var) {
+    double res = k.c0 * uc - k.rx * (w + e);
+    if (g.dim > 1) res -= k.ry * (s + n);
+    if (g.dim > 2) res -= k.rz * (bz + fz);
+    return res;
+  }
+  const long long fx = ((long long)z * g.ny + y) * (g.nx + 1) + x;
+  double res = gv.c0[idx] * uc - gv.cx[fx] * w - gv.cx[fx + 1] * e;
+  if (g.dim > 1) {
+    const long long fy = ((long long)z * (g.ny + 1) + y) * g.nx + x;
+    res -= gv.cy[fy] * s + gv.cy[fy + g.nx] * n;
+  }
+  if (g.dim > 2) res -= gv.cz[idx] * bz + gv.cz[idx + plane] * fz;
+  return res;
+}
+
+// --------------------------------------------------------------- reductions
+constexpr int RED_THREADS = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block sum of three values into part[3*blk + {0,1,2}] (fixed order).
+__device__ __forceinline__ void block_sum3(double v0, double v1, double v2, double* part, int blk) {
+  __shared__ double sh[3][RED_THREADS / 32];
+  v0 = warp_sum(v0);
+  v1 = warp_sum(v1);
+  v2 = warp_sum(v2);
+  const int wid = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (lane == 0) {
+    sh[0][wid] = v0;
+    sh[1][wid] = v1;
+    sh[2][wid] = v2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int i = 0; i < (int)(blockDim.x / 32); ++i) {
+      s0 += sh[0][i];
+      s1 += sh[1][i];
+      s2 += sh[2][i];
+    }
+    part[3 * blk] = s0;
+    part[3 * blk + 1] = s1;
+    part[3 * blk + 2] = s2;
+  }
+  __syncthreads();
+}
+
+// Sum of nblk block partials in a fixed order; identical result in every block.
+__device__ __forceinline__ void group_sum3(const double* part, int nblk, double& o0, double& o1,
+                                           double& o2) {
+  __shared__ double res[3];
+  if (threadIdx.x < 32) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int i = threadIdx.x; i < nblk; i += 32) {
+      s0 += __ldcg(part + 3 * i);
+      s1 += __ldcg(part + 3 * i + 1);
+      s2 += __ldcg(part + 3 * i + 2);
+    }
+    s0 = warp_sum(s0);
+    s1 = warp_sum(s1);
+    s2 = warp_sum(s2);
+    if (threadIdx.x == 0) {
+      res[0] = s0;
+      res[1] = s1;
+      res[2] = s2;
+    }
+  }
+  __syncthreads();
+  o0 = res[0];
+  o1 = res[1];
+  o2 = res[2];
+  __syncthreads();
+}
+
+__device__ __forceinline__ unsigned long long abs_bits(double d) {
+  return (unsigned long long)__double_as_longlong(fabs(d));
+}
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long other = __shfl_xor_sync(0xffffffffu, v, o);
+    v = other > v ? other : v;
+  }
+  return v;
+}
+
+// ------------------------------------------------------------ timing, flags
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Barrier over `nblk` co-resident blocks (a cooperative launch guarantees
+// co-residency).  Generation-counter scheme; the wait is bounded by
+// `deadline` (globaltimer ns): on expiry *err is set to 1 and the function
+// returns false in every thread of the block.  Never traps.
+struct TeamBarrier {
+  unsigned* count;
+  unsigned* gen;
+  int nblk;
+  unsigned long long deadline;
+  int* err;
+
+  __device__ bool sync() const {
+    __shared__ int timed_out;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      timed_out = 0;
+      if (nblk > 1) {
+        const unsigned g0 = ld_acquire_u32(gen);
+        __threadfence();
+        if (atomicAdd(count, 1u) == (unsigned)nblk - 1u) {
+          atomicExch(count, 0u);
+          __threadfence();
+          st_release_u32(gen, g0 + 1u);
+        } else {
+          unsigned spins = 0;
+          while (ld_acquire_u32(gen) == g0) {
+            if ((++spins & 63u) == 0 && globaltimer() > deadline) {
+              atomicExch(err, 1);
+              timed_out = 1;
+              break;
+            }
+            __nanosleep(32);
+          }
+        }
+      } else {
+        __threadfence();
+      }
+    }
+    __syncthreads();
+    return !timed_out;
+  }
+};
+
+// --------------------------------------------------------- conjugate gradients
+// Textbook CG for (I + dT A) x = b over a group of `nblk` blocks (this block
+// is number `blk`), stopping when ||r||_2 <= rtol ||b||_2, r == 0 or after
+// maxit iterations.  x0 may alias nothing it writes (x, r, p, q are the
+// group's workspace).  `abort_flag` (may be NULL) is sampled by block 0 at
+// every reduction and folded into the reduced values, so all blocks abandon
+// the solve at the same point.  Returns the iteration count, or -1 when
+// aborted / a barrier timed out.
+struct CgWork {
+  double* x;
+  double* r;
+  double* p;
+  double* q;
+  double* part;  // 2 parity buffers x 3 values x nblk
+};
+
+template <class Barrier>
+__device__ int cg_core(const Geom& g, const StencilConst& k, bool var, const StencilVar<double>& gv,
+                       const double* __restrict__ b, const double* __restrict__ x0, double rtol,
+                       int maxit, const CgWork& ws, const Barrier& bar, int nblk, int blk,
+                       const int* abort_flag) {
+  const long long M = g.M;
+  const long long t0 = blk * (long long)blockDim.x + threadIdx.x;
+  const long long nt = (long long)nblk * blockDim.x;
+  int parity = 0;
+  auto part = [&]() { return ws.part + (size_t)parity * 3 * nblk; };
+  auto flag = [&]() -> double {
+    return (abort_flag && blk == 0 && threadIdx.x == 0 && ld_acquire(abort_flag)) ? 1.0 : 0.0;
+  };
+  double s_rr = 0.0, s_bb = 0.0;
+  for (long long i = t0; i < M; i += nt) {
+    const double bi = b[i];
+    const double ri = bi - gop_at(g, k, var, gv, x0, i);
+    ws.x[i] = x0[i];
+    ws.r[i] = ri;
+    ws.p[i] = ri;
+    s_rr += ri * ri;
+    s_bb += bi * bi;
+  }
+  block_sum3(s_rr, s_bb, flag(), part(), blk);
+  if (!bar.sync()) return -1;
+  double rr, bb, ab;
+  group_sum3(part(), nblk, rr, bb, ab);
+  parity ^= 1;
+  if (ab != 0.0) return -1;
+  const double thresh = rtol * sqrt(bb);
+  int it = 0;
+  bool done = sqrt(rr) <= thresh || rr == 0.0 || maxit <= 0;
+  while (!done) {
+    double s_pq = 0.0;
+    for (long long i = t0; i < M; i += nt) {
+      const double qi = gop_at(g, k, var, gv, ws.p, i);
+      ws.q[i] = qi;
+      s_pq += ws.p[i] * qi;
+    }
+    block_sum3(s_pq, 0.0, flag(), part(), blk);
+    if (!bar.sync()) return -1;
+    double pq, u1;
+    group_sum3(part(), nblk, pq, u1, ab);
+    parity ^= 1;
+    if (ab != 0.0) return -1;
+    const double alpha = rr / pq;
+    double s_rn = 0.0;
+    for (long long i = t0; i < M; i += nt) {
+      ws.x[i] += alpha * ws.p[i];
+      const double ri = ws.r[i] - alpha * ws.q[i];
+      ws.r[i] = ri;
+      s_rn += ri * ri;
+    }
+    block_sum3(s_rn, 0.0, 0.0, part(), blk);
+    if (!bar.sync()) return -1;
+    double rr_new, u2;
+    group_sum3(part(), nblk, rr_new, u1, u2);
+    parity ^= 1;
+    ++it;
+    done = sqrt(rr_new) <= thresh || rr_new == 0.0 || it >= maxit;
+    if (!done) {
+      const double beta = rr_new / rr;
+      for (long long i = t0; i < M; i += nt) ws.p[i] = ws.r[i] + beta * ws.p[i];
+      rr = rr_new;
+      if (!bar.sync()) return -1;
+    }
+  }
+  return it;
+}
+
+}  // namespace pr

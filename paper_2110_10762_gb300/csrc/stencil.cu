@@ -1,0 +1,295 @@
+// Explicit-Euler fine propagator F (§3.1 F, §5.1 time stepping), batched over
+// time slices: one launch advances every state of the batch by one step
+//   u' = u - dt A_kappa u
+// written as u' = c0 u + sum_faces c_f u_q (zero Dirichlet: u_q = 0 outside).
+//
+// Layout: state c of the batch starts at c*M; x fastest.  A warp covers 32
+// consecutive x (coalesced rows); each thread walks a short column in y (2D)
+// or z (3D, 2.5D streaming) keeping the centre line in registers, so every
+// value is loaded from L2/HBM once per step and x/y neighbours come from L1.
+//
+// Precision: T is the arithmetic type.  Tin/Tout let the first and last step
+// of an FP32 fine solve read and write the FP64 states directly (the casts
+// of the mixed form are fused into those steps).
+#include "common.cuh"
+
+namespace pr {
+
+namespace {
+
+constexpr int BX = 32;
+constexpr int BY = 8;
+constexpr int RY = 4;   // rows per thread (2D)
+constexpr int ZC = 16;  // z planes per thread (3D)
+
+template <typename T, typename S>
+__device__ __forceinline__ T ld(const S* p) {
+  return static_cast<T>(__ldg(p));
+}
+
+// 1D and 2D.  DIM = 1 ignores y coupling (ny = 1).
+template <typename Tin, typename Tout, typename T, bool VAR, int DIM>
+__global__ void __launch_bounds__(BX* BY) step2d(const Tin* __restrict__ in, Tout* __restrict__ out,
+                                                 int nx, int ny, long long M, T c0, T rx, T ry,
+                                                 StencilVar<T> cv) {
+  const int x = blockIdx.x * BX + threadIdx.x;
+  const int y0 = (blockIdx.y * BY + threadIdx.y) * RY;
+  if (x >= nx || y0 >= ny) return;
+  const long long base = (long long)blockIdx.z * M;
+  const Tin* u = in + base;
+  Tout* o = out + base;
+  T s = (DIM > 1 && y0 > 0) ? ld<T>(u + (long long)(y0 - 1) * nx + x) : T(0);
+  T cur = ld<T>(u + (long long)y0 * nx + x);
+#pragma unroll
+  for (int j = 0; j < RY; ++j) {
+    const int y = y0 + j;
+    if (y >= ny) break;
+    const long long p = (long long)y * nx + x;
+    const T n = (DIM > 1 && y + 1 < ny) ? ld<T>(u + p + nx) : T(0);
+    const T w = x > 0 ? ld<T>(u + p - 1) : T(0);
+    const T e = x + 1 < nx ? ld<T>(u + p + 1) : T(0);
+    T res;
+    if (!VAR) {
+      res = c0 * cur + rx * (w + e);
+      if (DIM > 1) res += ry * (s + n);
+    } else {
+      const long long fx = (long long)y * (nx + 1) + x;
+      res = ld<T>(cv.c0 + p) * cur;
+      res += ld<T>(cv.cx + fx) * w;
+      res += ld<T>(cv.cx + fx + 1) * e;
+      if (DIM > 1) {
+        res += ld<T>(cv.cy + p) * s;
+        res += ld<T>(cv.cy + p + nx) * n;
+      }
+    }
+    o[p] = static_cast<Tout>(res);
+    s = cur;
+    cur = n;
+  }
+}
+
+template <typename Tin, typename Tout, typename T, bool VAR>
+__global__ void __launch_bounds__(BX* BY) step3d(const Tin* __restrict__ in, Tout* __restrict__ out,
+                                                 int nx, int ny, int nz, int zchunks, long long M,
+                                                 T c0, T rx, T ry, T rz, StencilVar<T> cv) {
+  const int x = blockIdx.x * BX + threadIdx.x;
+  const int y = blockIdx.y * BY + threadIdx.y;
+  const int slice = blockIdx.z / zchunks;
+  const int z0 = (blockIdx.z - slice * zchunks) * ZC;
+  if (x >= nx || y >= ny || z0 >= nz) return;
+  const long long plane = (long long)nx * ny;
+  const long long base = (long long)slice * M;
+  const Tin* u = in + base;
+  Tout* o = out + base;
+  const long long yx = (long long)y * nx + x;
+  T b = z0 > 0 ? ld<T>(u + (z0 - 1) * plane + yx) : T(0);
+  T cur = ld<T>(u + z0 * plane + yx);
+#pragma unroll 4
+  for (int j = 0; j < ZC; ++j) {
+    const int z = z0 + j;
+    if (z >= nz) break;
+    const long long p = z * plane + yx;
+    const T f = z + 1 < nz ? ld<T>(u + p + plane) : T(0);
+    const T w = x > 0 ? ld<T>(u + p - 1) : T(0);
+    const T e = x + 1 < nx ? ld<T>(u + p + 1) : T(0);
+    const T s = y > 0 ? ld<T>(u + p - nx) : T(0);
+    const T n = y + 1 < ny ? ld<T>(u + p + nx) : T(0);
+    T res;
+    if (!VAR) {
+      res = c0 * cur + rx * (w + e) + ry * (s + n) + rz * (b + f);
+    } else {
+      const long long fx = ((long long)z * ny + y) * (nx + 1) + x;
+      const long long fy = ((long long)z * (ny + 1) + y) * nx + x;
+      res = ld<T>(cv.c0 + p) * cur;
+      res += ld<T>(cv.cx + fx) * w;
+      res += ld<T>(cv.cx + fx + 1) * e;
+      res += ld<T>(cv.cy + fy) * s;
+      res += ld<T>(cv.cy + fy + nx) * n;
+      res += ld<T>(cv.cz + p) * b;
+      res += ld<T>(cv.cz + p + plane) * f;
+    }
+    o[p] = static_cast<Tout>(res);
+    b = cur;
+    cur = f;
+  }
+}
+
+template <typename Tin, typename Tout, typename T>
+cudaError_t launch_step(const pr_ctx* c, const Tin* in, Tout* out, int count,
+                        const StencilVar<T>& cv) {
+  const Geom& g = c->g;
+  const T c0 = static_cast<T>(c->fst.c0), rx = static_cast<T>(c->fst.rx),
+          ry = static_cast<T>(c->fst.ry), rz = static_cast<T>(c->fst.rz);
+  dim3 blk(BX, BY);
+  if (g.dim <= 2) {
+    dim3 grd((g.nx + BX - 1) / BX, (g.ny + BY * RY - 1) / (BY * RY), count);
+    if (g.dim == 1) {
+      if (c->var_kappa)
+        step2d<Tin, Tout, T, true, 1><<<grd, blk, 0, c->stream>>>(in, out, g.nx, 1, g.M, c0, rx, ry, cv);
+      else
+        step2d<Tin, Tout, T, false, 1><<<grd, blk, 0, c->stream>>>(in, out, g.nx, 1, g.M, c0, rx, ry, cv);
+    } else {
+      if (c->var_kappa)
+        step2d<Tin, Tout, T, true, 2><<<grd, blk, 0, c->stream>>>(in, out, g.nx, g.ny, g.M, c0, rx, ry, cv);
+      else
+        step2d<Tin, Tout, T, false, 2><<<grd, blk, 0, c->stream>>>(in, out, g.nx, g.ny, g.M, c0, rx, ry, cv);
+    }
+  } else {
+    const int zchunks = (g.nz + ZC - 1) / ZC;
+    dim3 grd((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, count * zchunks);
+    if (c->var_kappa)
+      step3d<Tin, Tout, T, true><<<grd, blk, 0, c->stream>>>(in, out, g.nx, g.ny, g.nz, zchunks, g.M,
+                                                              c0, rx, ry, rz, cv);
+    else
+      step3d<Tin, Tout, T, false><<<grd, blk, 0, c->stream>>>(in, out, g.nx, g.ny, g.nz, zchunks, g.M,
+                                                               c0, rx, ry, rz, cv);
+  }
+  return cudaGetLastError();
+}
+
+// ---- variable-kappa coefficient construction (one thread per face / node)
+__device__ __forceinline__ long long ring_index(const Geom& g, int xr, int yr, int zr) {
+  if (g.dim == 1) return xr;
+  if (g.dim == 2) return (long long)yr * (g.nx + 2) + xr;
+  return ((long long)zr * (g.ny + 2) + yr) * (g.nx + 2) + xr;
+}
+
+// Face diffusivity kappa_f = (kappa_p + kappa_q)/2 scaled by s/h^2 for F (s = dt)
+// and G (s = dT).  Interior node (x,y,z) has ring coordinates (x+1, y+1, z+1)
+// along the axes that exist.
+__global__ void faces_kernel(Geom g, const double* __restrict__ kap, double sF, double sG,
+                             double* fcx, double* fcy, double* fcz, double* gcx, double* gcy,
+                             double* gcz) {
+  const long long nfx = (long long)(g.nx + 1) * g.ny * g.nz;
+  const long long nfy = g.dim > 1 ? (long long)g.nx * (g.ny + 1) * g.nz : 0;
+  const long long nfz = g.dim > 2 ? (long long)g.nx * g.ny * (g.nz + 1) : 0;
+  const int oy = g.dim > 1 ? 1 : 0, oz = g.dim > 2 ? 1 : 0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nfx + nfy + nfz;
+       t += (long long)gridDim.x * blockDim.x) {
+    if (t < nfx) {
+      const int xf = t % (g.nx + 1);
+      const long long line = t / (g.nx + 1);
+      const int y = line % g.ny, z = line / g.ny;
+      const double kf = 0.5 * (kap[ring_index(g, xf, y + oy, z + oz)] +
+                               kap[ring_index(g, xf + 1, y + oy, z + oz)]);
+      fcx[t] = sF * kf / (g.hx * g.hx);
+      gcx[t] = sG * kf / (g.hx * g.hx);
+    } else if (t < nfx + nfy) {
+      const long long q = t - nfx;
+      const int x = q % g.nx;
+      const long long r = q / g.nx;
+      const int yf = r % (g.ny + 1), z = r / (g.ny + 1);
+      const double kf = 0.5 * (kap[ring_index(g, x + 1, yf, z + oz)] +
+                               kap[ring_index(g, x + 1, yf + 1, z + oz)]);
+      fcy[q] = sF * kf / (g.hy * g.hy);
+      gcy[q] = sG * kf / (g.hy * g.hy);
+    } else {
+      const long long q = t - nfx - nfy;
+      const int x = q % g.nx;
+      const long long r = q / g.nx;
+      const int y = r % g.ny, zf = r / g.ny;
+      const double kf = 0.5 * (kap[ring_index(g, x + 1, y + 1, zf)] +
+                               kap[ring_index(g, x + 1, y + 1, zf + 1)]);
+      fcz[q] = sF * kf / (g.hz * g.hz);
+      gcz[q] = sG * kf / (g.hz * g.hz);
+    }
+  }
+}
+
+__global__ void diag_kernel(Geom g, const double* fcx, const double* fcy, const double* fcz,
+                            const double* gcx, const double* gcy, const double* gcz, double* f0,
+                            double* g0) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < g.M;
+       p += (long long)gridDim.x * blockDim.x) {
+    const int x = p % g.nx;
+    const long long r = p / g.nx;
+    const int y = r % g.ny, z = r / g.ny;
+    const long long fx = ((long long)z * g.ny + y) * (g.nx + 1) + x;
+    double sf = fcx[fx] + fcx[fx + 1];
+    double sg = gcx[fx] + gcx[fx + 1];
+    if (g.dim > 1) {
+      const long long fy = ((long long)z * (g.ny + 1) + y) * g.nx + x;
+      sf += fcy[fy] + fcy[fy + g.nx];
+      sg += gcy[fy] + gcy[fy + g.nx];
+    }
+    if (g.dim > 2) {
+      const long long plane = (long long)g.nx * g.ny;
+      sf += fcz[p] + fcz[p + plane];
+      sg += gcz[p] + gcz[p + plane];
+    }
+    f0[p] = 1.0 - sf;
+    g0[p] = 1.0 + sg;
+  }
+}
+
+__global__ void to_float_kernel(const double* __restrict__ a, float* __restrict__ b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    b[i] = static_cast<float>(a[i]);
+}
+
+}  // namespace
+
+cudaError_t build_var_coefficients(pr_ctx* c) {
+  const Geom& g = c->g;
+  const long long nfx = (long long)(g.nx + 1) * g.ny * g.nz;
+  const long long nfy = g.dim > 1 ? (long long)g.nx * (g.ny + 1) * g.nz : 0;
+  const long long nfz = g.dim > 2 ? (long long)g.nx * g.ny * (g.nz + 1) : 0;
+  const long long total = g.M + nfx + nfy + nfz;
+  cudaError_t e;
+  if ((e = cudaMalloc(&c->fcoef, total * sizeof(double))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&c->gcoef, total * sizeof(double))) != cudaSuccess) return e;
+  double* f0 = c->fcoef;
+  double* fx = f0 + g.M;
+  double* fy = fx + nfx;
+  double* fz = fy + nfy;
+  double* g0 = c->gcoef;
+  double* gx = g0 + g.M;
+  double* gy = gx + nfx;
+  double* gz = gy + nfy;
+  const int blocks = c->num_sms * 8;
+  faces_kernel<<<blocks, 256, 0, c->stream>>>(g, c->prob.kappa_dev, c->dt, c->dT, fx, fy, fz, gx, gy, gz);
+  diag_kernel<<<blocks, 256, 0, c->stream>>>(g, fx, fy, fz, gx, gy, gz, f0, g0);
+  c->fvar = {f0, fx, nfy ? fy : nullptr, nfz ? fz : nullptr};
+  c->gvar = {g0, gx, nfy ? gy : nullptr, nfz ? gz : nullptr};
+  if (c->prob.f_prec == 32) {
+    if ((e = cudaMalloc(&c->fcoef32, total * sizeof(float))) != cudaSuccess) return e;
+    to_float_kernel<<<blocks, 256, 0, c->stream>>>(c->fcoef, c->fcoef32, total);
+    float* q0 = c->fcoef32;
+    float* qx = q0 + g.M;
+    float* qy = qx + nfx;
+    float* qz = qy + nfy;
+    c->fvar32 = {q0, qx, nfy ? qy : nullptr, nfz ? qz : nullptr};
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t explicit_fine(pr_ctx* c, const double* in, double* out, int count, int steps,
+                          int prec) {
+  if (count <= 0 || steps <= 0) return cudaSuccess;
+  cudaError_t e = cudaSuccess;
+  if (prec == 64) {
+    const double* src = in;
+    for (int s = 0; s < steps; ++s) {
+      double* dst = ((steps - 1 - s) % 2 == 0) ? out : c->tmp;
+      e = launch_step<double, double, double>(c, src, dst, count, c->fvar);
+      if (e != cudaSuccess) return e;
+      src = dst;
+    }
+    return e;
+  }
+  // FP32 steps, FP64 input and output
+  if (steps == 1) return launch_step<double, double, float>(c, in, out, count, c->fvar32);
+  e = launch_step<double, float, float>(c, in, c->f32a, count, c->fvar32);
+  if (e != cudaSuccess) return e;
+  const float* src = c->f32a;
+  for (int s = 1; s < steps - 1; ++s) {
+    float* dst = (src == c->f32a) ? c->f32b : c->f32a;
+    e = launch_step<float, float, float>(c, src, dst, count, c->fvar32);
+    if (e != cudaSuccess) return e;
+    src = dst;
+  }
+  return launch_step<float, double, float>(c, src, out, count, c->fvar32);
+}
+
+}  // namespace pr

@@ -1,0 +1,275 @@
+"""GPU parity of the fine/coarse propagators, the fused correction and
+synchronous Parareal (Algorithm 1) against the FP64 CPU oracle.
+
+Tolerances (relative L2 over the compared arrays):
+  FP64 path       1e-12  (different rounding order only)
+  mixed FP32 fine 1e-5   (FP32 steps, FP64 coarse/correction/test)
+  correction      bit-exact (same operation order in IEEE FP64)
+"""
+import numpy as np
+import pytest
+
+from oracle import heat
+from oracle.parareal import serial_fine, sync_parareal
+from synthetic import preset
+
+from .gpu_util import Ctx, dev, host, rel_l2, torch
+
+pr = pytest.importorskip("paper_2110_10762_gb300")
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+MIXED_TOL = 1e-5
+
+
+def small(name, **over):
+    p = preset(name, "small")
+    p.update(over)
+    return p
+
+
+CASES = {
+    "1d_thomas": lambda: small("heat1d_thomas"),
+    "1d_explicit": lambda: dict(small("heat1d_thomas"), f_scheme="explicit", g_solver="cg",
+                                dt=0.3 / 128 ** 2, g_rtol=1e-13),
+    "2d_const": lambda: small("heat2d_explicit", g_rtol=1e-13),
+    "2d_var": lambda: small("heat2d_inverse", g_rtol=1e-13),
+    "3d_const": lambda: small("heat3d_mixed", f_prec=64, g_rtol=1e-13),
+    "3d_var": lambda: small("heat3d_varkappa_async", f_prec=64, g_rtol=1e-13),
+}
+
+
+def oracle_props(p):
+    return heat.Propagators(p)
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_fine_propagator_batched(case):
+    p = CASES[case]()
+    rng = np.random.default_rng(11)
+    shape = tuple(reversed(p["n"]))
+    X = rng.standard_normal((p["N"],) + shape)
+    P = oracle_props(p)
+    with Ctx(p) as c:
+        xin = dev(X)
+        out = torch().empty_like(xin)
+        pr.parareal_fine(c.ctx, xin, out, p["N"])
+        got = host(out).reshape(X.shape)
+    for s in range(p["N"]):
+        assert rel_l2(got[s], P.F(X[s])) < FP64_TOL, s
+
+
+@pytest.mark.parametrize("case", ["2d_const", "3d_var"])
+def test_fine_propagator_mixed_precision(case):
+    p = CASES[case]()
+    p["f_prec"] = 32
+    rng = np.random.default_rng(12)
+    shape = tuple(reversed(p["n"]))
+    X = rng.standard_normal((p["N"],) + shape)
+    P = oracle_props(p)
+    with Ctx(p) as c:
+        xin = dev(X)
+        out = torch().empty_like(xin)
+        pr.parareal_fine(c.ctx, xin, out, p["N"])
+        got = host(out).reshape(X.shape)
+    for s in range(p["N"]):
+        err = rel_l2(got[s], P.F(X[s]))
+        assert err < MIXED_TOL, (s, err)
+        assert err > 1e-12  # the steps really ran in FP32
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_coarse_propagator(case):
+    p = CASES[case]()
+    rng = np.random.default_rng(13)
+    shape = tuple(reversed(p["n"]))
+    b = rng.standard_normal(shape)
+    x0 = b + 0.1 * rng.standard_normal(shape)
+    P = oracle_props(p)
+    ref, ref_it = P.G(b, x0=x0)
+    with Ctx(p) as c:
+        out = torch().empty(c.M, dtype=torch().float64, device="cuda")
+        it = pr.parareal_coarse(c.ctx, dev(b), dev(x0), out)
+        got = host(out)
+    assert rel_l2(got, ref) < FP64_TOL
+    if p.get("g_solver") != "thomas":
+        assert abs(it - ref_it) <= 2, (it, ref_it)
+        # residual of the GPU solution, measured by the oracle's operator
+        r = b - (got.reshape(shape) + P.dT * heat.apply_A(got.reshape(shape), P.h, P.kappa))
+        assert np.linalg.norm(r) <= 1e-12 * np.linalg.norm(b) * 10
+
+
+def test_correction_is_bit_exact():
+    p = CASES["2d_const"]()
+    rng = np.random.default_rng(14)
+    M = int(np.prod(p["n"]))
+    wn, v, wo, lam = (rng.standard_normal(M) * s for s in (1.0, 1e-3, 1.0, 1.0))
+    expect = (wn + v) - wo
+    with Ctx(p) as c:
+        lam_t = dev(lam)
+        d = pr.parareal_correct(c.ctx, dev(wn), dev(v), dev(wo), lam_t)
+        got = host(lam_t)
+    assert np.array_equal(got, expect)
+    assert d == np.max(np.abs(expect - lam))
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_sync_parareal_matches_oracle(case):
+    p = CASES[case]()
+    p["tol"] = 1e-9 if case != "1d_thomas" else 1e-10
+    ref = sync_parareal(p)
+    with Ctx(p) as c:
+        lam = c.lam()
+        code, st = pr.parareal_run_sync(c.ctx, lam)
+        got = host(lam).reshape(ref.lam.shape)
+        ks, ds = pr.parareal_slice_stats(c.ctx, p["N"])
+    assert st.iterations == ref.k, (st.iterations, ref.k)
+    assert rel_l2(got, ref.lam) < FP64_TOL
+    # increments near convergence are differences of O(1) states: compare on the state scale
+    np.testing.assert_allclose(st.max_delta, np.max(ref.deltas[-1]), rtol=0,
+                               atol=1e-12 * np.max(np.abs(ref.lam)))
+    assert st.fine_lups == sum(p["N"] - k for k in range(ref.k)) * int(np.prod(p["n"])) * p["f_steps"]
+
+
+@pytest.mark.parametrize("case", ["2d_const", "3d_var", "1d_thomas"])
+def test_sync_every_iterate_matches_oracle(case):
+    """Run with max_iter = k for each k and compare lam^k (iterate-level parity)."""
+    p = CASES[case]()
+    ref = sync_parareal(p, tol=0.0, record=True)
+    with Ctx(p) as c:
+        for k in range(1, p["N"] + 1):
+            c.prob.max_iter = k
+            c.prob.tol = 0.0
+            pr.parareal_set_problem(c.ctx, c.prob)
+            lam = c.lam()
+            pr.parareal_run_sync(c.ctx, lam)
+            assert rel_l2(host(lam), ref.iterates[k]) < FP64_TOL, k
+
+
+@pytest.mark.parametrize("case", ["2d_const", "3d_const"])
+def test_sync_mixed_precision_against_fp64_oracle(case):
+    p = CASES[case]()
+    p["f_prec"] = 32
+    p["tol"] = 1e-7
+    ref = sync_parareal(p)
+    with Ctx(p) as c:
+        lam = c.lam()
+        pr.parareal_run_sync(c.ctx, lam)
+        got = host(lam)
+    assert rel_l2(got, ref.lam) < MIXED_TOL
+
+
+@pytest.mark.parametrize("case", ["2d_var", "1d_thomas", "3d_const"])
+def test_finite_termination_equals_serial_fine(case):
+    p = CASES[case]()
+    p["g_rtol"] = 1e-4   # inexact coarse solves: termination holds for any G
+    ref = serial_fine(p)
+    with Ctx(p) as c:
+        lam = c.lam()
+        code, st = pr.parareal_run_sync(c.ctx, lam)
+        assert st.iterations == p["N"]
+        sf = c.lam()
+        pr.parareal_serial_fine(c.ctx, sf)
+        assert rel_l2(host(sf), ref) < FP64_TOL
+        assert rel_l2(host(lam), ref) < FP64_TOL
+
+
+def test_run_sync_host_buffers_match_device_run():
+    p = CASES["2d_const"]()
+    p["tol"] = 1e-8
+    with Ctx(p) as c:
+        lam = c.lam()
+        pr.parareal_run_sync(c.ctx, lam)
+        t = torch()
+        u0h = t.from_numpy(p["u0"].reshape(-1).copy()).pin_memory()
+        out = t.empty((p["N"] + 1) * c.M, dtype=t.float64).pin_memory()
+        code, st = pr.parareal_run_sync_host(c.ctx, u0h, out)
+        assert np.array_equal(out.numpy(), host(lam))
+
+
+# ------------------------------------------------------------------ edges
+def test_single_slice_single_point_1d():
+    p = dict(dim=1, n=(1,), h=(0.5,), N=1, f_steps=3, dt=1e-3, f_scheme="implicit",
+             g_solver="thomas", u0=np.array([0.7]), tol=0.0)
+    ref = sync_parareal(p)
+    with Ctx(p) as c:
+        lam = c.lam()
+        pr.parareal_run_sync(c.ctx, lam)
+        assert rel_l2(host(lam), ref.lam) < FP64_TOL
+
+
+@pytest.mark.parametrize("n", [(2,), (3,), (5,), (33,), (64,), (65,), (1000,)])
+def test_thomas_partition_ragged_sizes(n):
+    rng = np.random.default_rng(n[0])
+    p = dict(dim=1, n=n, h=(1.0 / (n[0] + 1),), N=3, f_steps=4, dt=2e-3, f_scheme="implicit",
+             g_solver="thomas", u0=rng.standard_normal(n), tol=0.0,
+             kappa=np.exp(rng.standard_normal(n[0] + 2)))
+    P = oracle_props(p)
+    X = rng.standard_normal((3,) + n)
+    with Ctx(p) as c:
+        xin = dev(X)
+        out = torch().empty_like(xin)
+        pr.parareal_fine(c.ctx, xin, out, 3)
+        got = host(out).reshape(X.shape)
+    for s in range(3):
+        assert rel_l2(got[s], P.F(X[s])) < FP64_TOL
+
+
+@pytest.mark.parametrize("n", [(1, 1), (33, 1), (1, 40), (31, 33)])
+def test_explicit_ragged_tiles_2d(n):
+    rng = np.random.default_rng(5)
+    p = dict(dim=2, n=n, h=tuple(1.0 / (m + 1) for m in n), N=2, f_steps=5,
+             dt=0.2 * min(1.0 / (m + 1) for m in n) ** 2, f_scheme="explicit", g_solver="cg",
+             g_rtol=1e-13, u0=rng.standard_normal(tuple(reversed(n))), tol=0.0)
+    P = oracle_props(p)
+    X = rng.standard_normal((2,) + tuple(reversed(n)))
+    with Ctx(p) as c:
+        xin = dev(X)
+        out = torch().empty_like(xin)
+        pr.parareal_fine(c.ctx, xin, out, 2)
+        got = host(out).reshape(X.shape)
+    for s in range(2):
+        assert rel_l2(got[s], P.F(X[s])) < FP64_TOL
+
+
+def test_invalid_problems_are_rejected():
+    p = CASES["2d_const"]()
+    t = torch()
+    u0 = dev(p["u0"])
+    ctx = pr.parareal_create(0, t.cuda.current_stream())
+    try:
+        lam = t.zeros(10, dtype=t.float64, device="cuda")
+        with pytest.raises(pr.PararealError) as e:
+            pr.parareal_run_sync(ctx, lam)
+        assert e.value.code == pr.PR_ESTATE
+        from .gpu_util import problem_struct
+        bad = [dict(N=0), dict(dim=4), dict(f_steps=0), dict(T=-1.0),
+               dict(f_prec=16), dict(g_solver=pr.PR_SOLVER_THOMAS)]
+        for over in bad:
+            s = problem_struct(p, u0, None, **over)
+            with pytest.raises(pr.PararealError) as e:
+                pr.parareal_set_problem(ctx, s)
+            assert e.value.code == pr.PR_EINVAL, over
+        # unstable explicit step: dt = 0.35 h^2 in 2D gives dt*lambda_max near 2.8 > 2
+        s = problem_struct(p, u0, None, T=p["N"] * p["f_steps"] * 0.35 * (1.0 / (p["n"][0] + 1)) ** 2)
+        with pytest.raises(pr.PararealError) as e:
+            pr.parareal_set_problem(ctx, s)
+        assert e.value.code == pr.PR_EINVAL
+        # misaligned device pointer
+        s = problem_struct(p, u0, None)
+        s.u0_dev = s.u0_dev + 8
+        with pytest.raises(pr.PararealError):
+            pr.parareal_set_problem(ctx, s)
+    finally:
+        pr.parareal_destroy(ctx)
+
+
+def test_notconv_status_when_max_iter_stops_early():
+    p = CASES["2d_const"]()
+    p["tol"] = 1e-14
+    p["max_iter"] = 2
+    with Ctx(p) as c:
+        lam = c.lam()
+        code, st = pr.parareal_run_sync(c.ctx, lam)
+        assert code == pr.PR_ENOTCONV and st.iterations == 2 and not st.converged
