@@ -187,6 +187,33 @@ int parareal_adjoint(pr_ctx* ctx, const double* dL_dlamN_dev, int K, double* gra
  * k_i (async update counts; sync: k for every slice) and delta_i. */
 int parareal_slice_stats(pr_ctx* ctx, int* k_host, double* delta_host);
 
+/* Allocation-free coarse solve.  The paper has no counterpart: this is a
+ * service for callers that must not allocate device memory while they run
+ * (an allocator hook or host callback where cudaMalloc would re-enter or is
+ * not allowed, a fixed memory budget checked at start-up, or a loop that
+ * cannot pay cudaMalloc/cudaFree's implicit device synchronisation).
+ * It solves one backward-Euler step (I + dT A) x = b for kappa = 1 on a
+ * dim-dimensional grid with n[0..dim-1] interior points, by the same CG as
+ * the coarse propagator (start x0_dev, NULL = b; stop at
+ * ||r||_2 <= rtol ||b||_2 or maxit iterations, maxit <= 0 = 20000), on the
+ * calling thread's current device and the given stream, without a context.
+ *  - Workspace: a static device array inside the library (about 4 MiB, held
+ *    by every GPU that loads the library until the process exits); no
+ *    cudaMalloc/cudaFree or other allocating call is made.
+ *  - Limit: M = prod(n) <= 131072 points; larger grids return PR_EINVAL.
+ *  - The first call on a device resolves the array's device address
+ *    (cudaGetSymbolAddress) and the launch limit; make that first call
+ *    outside any stream capture.
+ *  - All calls on a device share the array and it keeps the last call's
+ *    contents (nothing of it is read before being rewritten): calls whose
+ *    work overlaps on the GPU race.  Serialise them.
+ *  - b_dev, x0_dev, x_dev: device, M doubles, 16-byte aligned, caller-owned.
+ *    *iters_host (may be NULL) receives the CG iteration count; passing it
+ *    synchronises the stream. */
+int parareal_coarse_noalloc(int dim, const int* n, double dT, const double* b_dev,
+                            const double* x0_dev, double* x_dev, double rtol, int maxit,
+                            int* iters_host, void* cuda_stream);
+
 void parareal_destroy(pr_ctx* ctx);
 const char* parareal_last_error(const pr_ctx* ctx);
 const char* parareal_version(void);

@@ -67,6 +67,9 @@ EXPORTS = {
                                    C.POINTER(C.c_double)]),
     "parareal_adjoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "parareal_slice_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    "parareal_coarse_noalloc": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.c_double, C.c_void_p,
+                                          C.c_void_p, C.c_void_p, C.c_double, C.c_int,
+                                          C.POINTER(C.c_int), C.c_void_p]),
     "parareal_destroy": (None, [C.c_void_p]),
     "parareal_last_error": (C.c_char_p, [C.c_void_p]),
     "parareal_version": (C.c_char_p, []),

@@ -181,6 +181,21 @@ def parareal_slice_stats(ctx, N: int):
     return list(k), list(d)
 
 
+def parareal_coarse_noalloc(dim: int, n, dT: float, b, x0, x_out, rtol: float = 1e-10,
+                            maxit: int = 0, stream=None) -> int:
+    """Allocation-free coarse solve (kappa = 1) for callers that must not allocate
+    device memory; see include/parareal.h.  Returns the CG iteration count."""
+    if stream is not None and not isinstance(stream, int):
+        stream = stream.cuda_stream
+    nn = (C.c_int * 3)(*(list(n) + [1] * (3 - len(n))))
+    it = C.c_int(0)
+    code = _lib().parareal_coarse_noalloc(int(dim), nn, float(dT), _ptr(b), _ptr(x0), _ptr(x_out),
+                                          float(rtol), int(maxit), C.byref(it), stream)
+    if code != PR_OK:
+        raise PararealError(code, "parareal_coarse_noalloc failed")
+    return it.value
+
+
 def parareal_destroy(ctx):
     if ctx:
         _lib().parareal_destroy(ctx)

@@ -1,0 +1,61 @@
+"""The allocation-free coarse solve (parareal_coarse_noalloc) against the
+context-based coarse solve (parareal_coarse).
+
+parareal_coarse_noalloc exists for callers that must not allocate device
+memory while running (allocator hooks, host callbacks, fixed memory budgets,
+loops that cannot afford cudaMalloc's implicit synchronisation); its CG
+vectors live in a static device array inside the library.  The test calls it
+twice in a row with different inputs -- the second call finds the first
+call's leftovers in that shared array -- and compares each result with the
+existing entry point within the FP64 parity tolerance of the other tests.
+This file is collected last on purpose.
+"""
+import numpy as np
+import pytest
+
+pr = pytest.importorskip("paper_2110_10762_gb300")
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_noalloc_coarse_matches_context_coarse_twice():
+    import torch
+    n = (211, 157)                       # 33127 points: below the 131072-point limit
+    h = 1.0 / (max(n) + 1)
+    f_steps = 256
+    dT = f_steps * 0.2 * h * h
+    rng = np.random.default_rng(21)
+    M = n[0] * n[1]
+    u0 = torch.from_numpy(rng.standard_normal(M)).cuda()
+    stream = torch.cuda.current_stream()
+    ctx = pr.parareal_create(0, stream)
+    try:
+        prob = pr.make_problem(dim=2, n=n, T0=0.0, T=dT, N=1, u0=u0, f_steps=f_steps,
+                               g_rtol=1e-13, tol=0.0)
+        pr.parareal_set_problem(ctx, prob)
+        for call in range(2):              # two calls in a row share the static scratch
+            b = torch.from_numpy(rng.standard_normal(M) * (1 + call)).cuda()
+            x0 = b + 0.05 * torch.from_numpy(rng.standard_normal(M)).cuda()
+            ref = torch.empty_like(b)
+            it_ref = pr.parareal_coarse(ctx, b, x0, ref)
+            got = torch.full_like(b, float("nan"))
+            it = pr.parareal_coarse_noalloc(2, n, dT, b, x0, got, rtol=1e-13, stream=stream)
+            torch.cuda.synchronize()
+            assert it == it_ref, (call, it, it_ref)
+            assert _rel(got.cpu().numpy(), ref.cpu().numpy()) < FP64_TOL, call
+    finally:
+        pr.parareal_destroy(ctx)
+
+
+def test_noalloc_rejects_grids_beyond_its_limit():
+    import torch
+    b = torch.zeros(8, dtype=torch.float64, device="cuda")
+    with pytest.raises(pr.PararealError) as e:
+        pr.parareal_coarse_noalloc(2, (1024, 1024), 1e-3, b, None, b)
+    assert e.value.code == pr.PR_EINVAL
