@@ -159,13 +159,16 @@ def make_async_opts(paper_literal=False, timeout_s=60.0, delays=None, delay_unit
 
 
 def parareal_run_async(ctx, opts: pr_async_opts, lam_out, log_cap: int = 0):
-    """Returns (status, stats, events) with events a list of pr_event."""
+    """Returns (status, stats, events) with events a list of pr_event; status is
+    PR_OK, PR_ETIMEOUT or PR_ELOGFULL (other failures raise PararealError)."""
     st = pr_stats()
     log = (pr_event * max(int(log_cap), 1))()
     n = C.c_size_t(0)
-    code = _check(ctx, _lib().parareal_run_async(ctx, C.byref(opts), _ptr(lam_out), C.byref(st),
-                                                  log if log_cap else None, int(log_cap),
-                                                  C.byref(n)))
+    code = _lib().parareal_run_async(ctx, C.byref(opts), _ptr(lam_out), C.byref(st),
+                                     log if log_cap else None, int(log_cap), C.byref(n))
+    if code not in (PR_OK, _abi.PR_ETIMEOUT, _abi.PR_ELOGFULL):
+        _check(ctx, code)
+    # a run stopped by its time limit or by a full log still returns its state and log
     return code, st, [log[i] for i in range(n.value)] if log_cap else []
 
 

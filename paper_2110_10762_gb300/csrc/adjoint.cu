@@ -1,10 +1,245 @@
-// Discrete adjoint of synchronous Parareal.
-#include "common.cuh"
+// Discrete adjoint (reverse mode) of K synchronous Parareal iterations
+// (Algorithm 1 of §4.1 with the prefix frozen and no early stop; Eq. (11)),
+// for L = L(lambda_N^K): given dL/dlambda_N it returns dL/du0 and dL/dkappa.
+//
+// Structure (mirrors the forward pass):
+//  * forward: predictor and K iterations with every iterate lambda^k and
+//    coarse value w^k kept as a checkpoint (slice-boundary states only);
+//  * reverse, iteration k = K-1..0:
+//      - sequential coarse sweep i = N..k+1: the correction's adjoint
+//        (wbar_i^{k+1} += g, wbar_i^k -= g with g = lambar_i^{k+1}), then
+//        G^T = G by CG on wbar_i^{k+1} feeding lambar_{i-1}^{k+1}, and the
+//        kappa-derivative of the coarse solve;
+//      - batched fine adjoint over the active slices: the n_f fine states are
+//        recomputed from the checkpoint lambda_{i-1}^k, then the transposed
+//        step (S^T = S, the same stencil) runs backward while the
+//        kappa-gradient kernel accumulates -dt * facegrad(a_{j+1}, u_j);
+//  * reverse predictor.
+// kappa-gradient of <a, A_kappa u>: every face (p,q) adds
+// (a_p - a_q)(u_p - u_q) / (2 h^2) to both of its nodes (boundary ring
+// included); the kernel gathers per node, so it is deterministic and needs
+// no atomics.
+#include <algorithm>
+
+#include "device.cuh"
 
 namespace pr {
+namespace {
 
-int run_adjoint(pr_ctx* c, const double*, int, double*, double*) {
-  return fail(c, PR_ESTATE, "adjoint path not built");
+__global__ void axpy_kernel(double* __restrict__ y, const double* __restrict__ x, double a,
+                            long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] += a * x[i];
+}
+
+__device__ __forceinline__ double padded_val(const Geom& g, const double* u, int xr, int yr, int zr) {
+  if (xr < 1 || xr > g.nx) return 0.0;
+  if (g.dim > 1 && (yr < 1 || yr > g.ny)) return 0.0;
+  if (g.dim > 2 && (zr < 1 || zr > g.nz)) return 0.0;
+  const int y = g.dim > 1 ? yr - 1 : 0;
+  const int z = g.dim > 2 ? zr - 1 : 0;
+  return u[((long long)z * g.ny + y) * g.nx + (xr - 1)];
+}
+
+// kbar[node] += scale * sum_{s < count} sum_{faces f of node} (a_s diff)(u_s diff) / (2 h^2)
+__global__ void facegrad_kernel(Geom g, double* __restrict__ kbar, const double* __restrict__ a,
+                                const double* __restrict__ u, int count, double scale) {
+  const int nxr = g.nx + 2;
+  const int nyr = g.dim > 1 ? g.ny + 2 : 1;
+  const int nzr = g.dim > 2 ? g.nz + 2 : 1;
+  const long long total = (long long)nxr * nyr * nzr;
+  const double ih[3] = {0.5 / (g.hx * g.hx), 0.5 / (g.hy * g.hy), 0.5 / (g.hz * g.hz)};
+  const int n[3] = {g.nx, g.ny, g.nz};
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < total;
+       r += (long long)gridDim.x * blockDim.x) {
+    int c[3];
+    c[0] = r % nxr;
+    const long long rest = r / nxr;
+    c[1] = g.dim > 1 ? (int)(rest % nyr) : 1;
+    c[2] = g.dim > 2 ? (int)(rest / nyr) : 1;
+    double acc = 0.0;
+    for (int ax = 0; ax < g.dim; ++ax) {
+      bool others_inside = true;
+      for (int b = 0; b < g.dim; ++b)
+        if (b != ax && (c[b] < 1 || c[b] > n[b])) others_inside = false;
+      if (!others_inside) continue;
+      for (int side = 0; side < 2; ++side) {
+        // face between padded positions lo and lo+1 along ax
+        const int lo = side == 0 ? c[ax] - 1 : c[ax];
+        if (lo < 0 || lo > n[ax]) continue;
+        int plo[3] = {c[0], c[1], c[2]}, phi[3] = {c[0], c[1], c[2]};
+        plo[ax] = lo;
+        phi[ax] = lo + 1;
+        for (int s = 0; s < count; ++s) {
+          const double* as = a + (long long)s * g.M;
+          const double* us = u + (long long)s * g.M;
+          const double da = padded_val(g, as, phi[0], phi[1], phi[2]) - padded_val(g, as, plo[0], plo[1], plo[2]);
+          const double du = padded_val(g, us, phi[0], phi[1], phi[2]) - padded_val(g, us, plo[0], plo[1], plo[2]);
+          acc += ih[ax] * da * du;
+        }
+      }
+    }
+    kbar[r] += scale * acc;
+  }
+}
+
+long long ring_count(const Geom& g) {
+  return (long long)(g.nx + 2) * (g.dim > 1 ? g.ny + 2 : 1) * (g.dim > 2 ? g.nz + 2 : 1);
+}
+
+}  // namespace
+
+int run_adjoint(pr_ctx* c, const double* gN, int K, double* grad_u0, double* grad_kappa) {
+  const pr_problem& p = c->prob;
+  if (p.f_scheme != PR_EXPLICIT_EULER || p.g_solver != PR_SOLVER_CG || p.f_prec != 64)
+    return fail(c, PR_EINVAL, "adjoint needs the FP64 explicit fine scheme and the CG coarse solver");
+  const Geom& g = c->g;
+  const long long M = g.M;
+  const int N = p.N, nf = p.f_steps;
+  const bool var = c->var_kappa;
+  if (grad_kappa && !var) return fail(c, PR_EINVAL, "grad_kappa needs a variable-kappa problem");
+  const long long Mr = ring_count(g);
+  const size_t traj = (size_t)(K + 1) * (N + 1) * M;
+  const size_t words = 4 * traj + (size_t)std::max(nf - 1, 1) * N * M + 2 * (size_t)N * M + M +
+                       (var ? (size_t)Mr : 0);
+  const size_t bytes = words * sizeof(double);
+  if (c->adj_ws_bytes < bytes) {
+    if (c->adj_ws) cudaFree(c->adj_ws);
+    c->adj_ws = nullptr;
+    c->adj_ws_bytes = 0;
+    PR_CUDA(c, cudaMalloc(&c->adj_ws, bytes));
+    c->adj_ws_bytes = bytes;
+  }
+  double* base = static_cast<double*>(c->adj_ws);
+  double* lam = base;
+  double* wv = lam + traj;
+  double* lb = wv + traj;
+  double* wb = lb + traj;
+  double* states = wb + traj;
+  double* abuf0 = states + (size_t)std::max(nf - 1, 1) * N * M;
+  double* abuf1 = abuf0 + (size_t)N * M;
+  double* zbuf = abuf1 + (size_t)N * M;
+  double* kbar = var ? zbuf + M : nullptr;
+  auto L = [&](double* arr, int k, int i) { return arr + ((size_t)k * (N + 1) + i) * M; };
+  const int blocks = c->num_sms * 8;
+  auto axpy = [&](double* y, const double* x, double a, long long n) {
+    axpy_kernel<<<blocks, 256, 0, c->stream>>>(y, x, a, n);
+    return cudaGetLastError();
+  };
+  auto G = [&](const double* b, double* out) {
+    CgArgs a{};
+    a.b = b;
+    a.x0 = b;
+    a.out = out;
+    a.iters = c->cg_iters_dev;
+    a.mode = CG_PLAIN;
+    return cg_solve(c, a);
+  };
+  unsigned long long* dscratch = c->delta_dev;
+
+  // ------------------------------------------------ forward with checkpoints
+  PR_CUDA(c, cudaMemcpyAsync(L(lam, 0, 0), p.u0_dev, M * sizeof(double), cudaMemcpyDeviceToDevice,
+                             c->stream));
+  for (int i = 1; i <= N; ++i) {
+    CgArgs a{};
+    a.b = L(lam, 0, i - 1);
+    a.x0 = a.b;
+    a.out = L(wv, 0, i);
+    a.lam = L(lam, 0, i);
+    a.iters = c->cg_iters_dev;
+    a.mode = CG_PREDICTOR;
+    PR_CUDA(c, cg_solve(c, a));
+  }
+  for (int k = 0; k < K; ++k) {
+    PR_CUDA(c, cudaMemcpyAsync(L(lam, k + 1, 0), L(lam, k, 0), (size_t)(N + 1) * M * sizeof(double),
+                               cudaMemcpyDeviceToDevice, c->stream));
+    PR_CUDA(c, cudaMemcpyAsync(L(wv, k + 1, 0), L(wv, k, 0), (size_t)(N + 1) * M * sizeof(double),
+                               cudaMemcpyDeviceToDevice, c->stream));
+    PR_CUDA(c, explicit_fine(c, L(lam, k, k), c->v + (size_t)k * M, N - k, nf, 64));
+    for (int i = k + 1; i <= N; ++i) {
+      double* vi = c->v + (size_t)(i - 1) * M;
+      if (i - 1 > k) {
+        CgArgs a{};
+        a.b = L(lam, k + 1, i - 1);
+        a.x0 = L(wv, k + 1, i);
+        a.out = L(wv, k + 1, i);
+        a.lam = L(lam, k + 1, i);
+        a.v = vi;
+        a.delta = dscratch;
+        a.iters = c->cg_iters_dev;
+        a.mode = CG_CORRECT;
+        PR_CUDA(c, cg_solve(c, a));
+      } else {
+        PR_CUDA(c, cudaMemsetAsync(dscratch, 0, sizeof(unsigned long long), c->stream));
+        PR_CUDA(c, correct(c, L(wv, k + 1, i), vi, L(wv, k, i), L(lam, k + 1, i), dscratch));
+      }
+    }
+  }
+
+  // ------------------------------------------------------------- reverse
+  PR_CUDA(c, cudaMemsetAsync(lb, 0, 2 * traj * sizeof(double), c->stream));  // lb and wb
+  if (var) PR_CUDA(c, cudaMemsetAsync(kbar, 0, Mr * sizeof(double), c->stream));
+  PR_CUDA(c, cudaMemcpyAsync(L(lb, K, N), gN, M * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  for (int k = K - 1; k >= 0; --k) {
+    // coarse sweep in reverse order
+    for (int i = N; i >= k + 1; --i) {
+      const double* gk = L(lb, k + 1, i);
+      PR_CUDA(c, axpy(L(wb, k + 1, i), gk, 1.0, M));
+      PR_CUDA(c, axpy(L(wb, k, i), gk, -1.0, M));
+      if (i - 1 > k) {
+        PR_CUDA(c, G(L(wb, k + 1, i), zbuf));
+        PR_CUDA(c, axpy(L(lb, k + 1, i - 1), zbuf, 1.0, M));
+        if (var) {
+          facegrad_kernel<<<blocks, 256, 0, c->stream>>>(g, kbar, zbuf, L(wv, k + 1, i), 1, -c->dT);
+          PR_CUDA(c, cudaGetLastError());
+        }
+      } else {
+        PR_CUDA(c, axpy(L(wb, k, i), L(wb, k + 1, i), 1.0, M));
+      }
+    }
+    // frozen prefix (slices 0..k): lambda_i^{k+1} = lambda_i^k
+    PR_CUDA(c, axpy(L(lb, k, 0), L(lb, k + 1, 0), 1.0, (long long)(k + 1) * M));
+    PR_CUDA(c, axpy(L(wb, k, 0), L(wb, k + 1, 0), 1.0, (long long)(k + 1) * M));
+    // batched fine adjoint for i = k+1..N: inputs lambda_{i-1}^k, vbar_i = lambar_i^{k+1}
+    const int count = N - k;
+    const double* x0 = L(lam, k, k);
+    for (int j = 1; j < nf; ++j) {
+      const double* src = j == 1 ? x0 : states + (size_t)(j - 2) * N * M;
+      PR_CUDA(c, explicit_step64(c, src, states + (size_t)(j - 1) * N * M, count));
+    }
+    PR_CUDA(c, cudaMemcpyAsync(abuf0, L(lb, k + 1, k + 1), (size_t)count * M * sizeof(double),
+                               cudaMemcpyDeviceToDevice, c->stream));
+    double* a = abuf0;
+    double* b = abuf1;
+    for (int j = nf - 1; j >= 0; --j) {
+      const double* uj = j == 0 ? x0 : states + (size_t)(j - 1) * N * M;
+      if (var) {
+        facegrad_kernel<<<blocks, 256, 0, c->stream>>>(g, kbar, a, uj, count, -c->dt);
+        PR_CUDA(c, cudaGetLastError());
+      }
+      PR_CUDA(c, explicit_step64(c, a, b, count));
+      std::swap(a, b);
+    }
+    PR_CUDA(c, axpy(L(lb, k, k), a, 1.0, (long long)count * M));
+  }
+  // predictor in reverse
+  for (int i = N; i >= 1; --i) {
+    PR_CUDA(c, axpy(L(wb, 0, i), L(lb, 0, i), 1.0, M));
+    PR_CUDA(c, G(L(wb, 0, i), zbuf));
+    PR_CUDA(c, axpy(L(lb, 0, i - 1), zbuf, 1.0, M));
+    if (var) {
+      facegrad_kernel<<<blocks, 256, 0, c->stream>>>(g, kbar, zbuf, L(wv, 0, i), 1, -c->dT);
+      PR_CUDA(c, cudaGetLastError());
+    }
+  }
+  PR_CUDA(c, cudaMemcpyAsync(grad_u0, L(lb, 0, 0), M * sizeof(double), cudaMemcpyDeviceToDevice,
+                             c->stream));
+  if (grad_kappa)
+    PR_CUDA(c, cudaMemcpyAsync(grad_kappa, kbar, Mr * sizeof(double), cudaMemcpyDeviceToDevice,
+                               c->stream));
+  PR_CUDA(c, cudaStreamSynchronize(c->stream));
+  return PR_OK;
 }
 
 }  // namespace pr

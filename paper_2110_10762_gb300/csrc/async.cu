@@ -1,10 +1,608 @@
-// Asynchronous Parareal persistent kernel (Eq. (12), Algorithm 2).
-#include "common.cuh"
+// Asynchronous Parareal (Eq. (12), Algorithm 2 of §4.1) as one persistent
+// cooperative kernel.
+//
+// Work decomposition.  The grid is T teams of C co-resident CTAs.  Team t
+// owns slices t+1, t+1+T, ... and updates them one at a time; a team barrier
+// (bounded wait) separates the phases of an update.  There is no global
+// barrier: teams communicate only through the published versions of lam_i.
+//
+// One update of slice i (Algorithm 2's loop body), done by its team:
+//   vF := the version of lam_{i-1} held in the slice's snapshot xs_i
+//         (it is the coarse input of the previous update, so
+//          w_i = G(lam_{i-1}^{vF}) is already known)
+//   v   = F(xs_i)                                   fine propagation
+//   vG  = freshest visible version of lam_{i-1}     (>= vF)
+//   if vG > vF: xs_i := lam_{i-1}^{vG} (seqlock-checked copy),
+//               w_new = G(xs_i) by CG started from w_i
+//   else:       w_new = w_i  (unchanged input, no solve)
+//   lam_i^{k+1} = (w_new + v) - w_i;  delta_i = max |lam_i^{k+1} - lam_i^k|
+//   publish lam_i^{k+1} into ring slot (k+1) % R, then w_i := w_new.
+// A version becomes visible to the successor at publish time + an optional
+// injected delay (communication delay).  Each update is logged as
+// (i, k+1, vF, vG, ...), which is all the oracle needs to replay the run.
+//
+// A slice is re-updated only when a newer predecessor version is visible
+// (or always, in paper-literal mode).  The run stops when every slice has
+// updated at least once and its last increment is below tol, or when no
+// slice can change any more (quiescence: lam_i = F(lam_{i-1}) for all i),
+// or at the wall-clock limit (status PR_ETIMEOUT).  Every spin is bounded.
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "device.cuh"
 
 namespace pr {
+namespace {
 
-int run_async(pr_ctx* c, const pr_async_opts*, double*, pr_stats*, pr_event*, size_t, size_t*) {
-  return fail(c, PR_ESTATE, "asynchronous path not built");
+constexpr int ATHREADS = RED_THREADS;
+constexpr int RING = 3;
+
+enum { DEC_IDLE = 0, DEC_UPDATE = 1, DEC_STOP = 2 };
+enum { AST_OK = 0, AST_TIMEOUT = 1, AST_LOGFULL = 2, AST_BARRIER = 3 };
+
+struct AsyncDev {
+  Geom g;
+  int N, T, C;
+  int f_steps, f_prec;
+  bool var;
+  StencilConst fst, gst;
+  StencilVar<double> fv, gv;
+  StencilVar<float> fv32;
+  double rtol, tol;
+  int maxit;
+  int paper_literal, quiescence;
+  const double* u0;
+  // per slice (index i-1)
+  double* ring;                   // N * RING * M
+  int* ring_ver;                  // N * RING   (-1: empty or being written)
+  unsigned long long* ring_vis;   // N * RING   visible-at time (globaltimer ns)
+  int* latest;                    // N + 1      latest published version (slot 0: u0)
+  double* xs;                     // N * M      predecessor snapshot (next F input)
+  double* w;                      // N * M      coarse value G(xs)
+  int* xver;                      // N          version held in xs
+  int* kcount;                    // N          updates published
+  double* delta;                  // N          last increment
+  int* lastfg;                    // N          last update had vF == vG
+  // per team
+  double* tv;                     // T * M      fine result v
+  double* tcg;                    // T * 4 * M  CG x, r, p, q (FP64 fine ping-pong aliases r, p)
+  double* tpart;                  // T * 6 * C
+  unsigned* bar;                  // T * 2
+  int* ctrl;                      // T * 8  (two decision slots, seqlock words)
+  unsigned long long* tdelta;     // T
+  // global
+  int* stop;
+  int* status;
+  int* barrier_err;
+  unsigned long long* log_count;
+  pr_event* log;
+  long long log_cap;
+  const int* delays;
+  int delay_cols;
+  double delay_unit_ns;
+  unsigned long long timeout_ns;  // wall-clock limit, counted from each block's start
+};
+
+__device__ __forceinline__ long long slice_off(const AsyncDev& a, int i) {
+  return (long long)(i - 1) * a.g.M;
+}
+__device__ __forceinline__ double* ring_slot(const AsyncDev& a, int i, int slot) {
+  return a.ring + ((long long)(i - 1) * RING + slot) * a.g.M;
+}
+
+// Freshest version of lam_{j} visible at `now` (j >= 1); -1 if none; slot in *slot.
+__device__ int freshest_visible(const AsyncDev& a, int j, unsigned long long now, int* slot) {
+  int best = -1;
+  for (int s = 0; s < RING; ++s) {
+    const int v = ld_acquire(a.ring_ver + (j - 1) * RING + s);
+    if (v < 0 || v <= best) continue;
+    const unsigned long long vis = ld_acquire_u64(a.ring_vis + (j - 1) * RING + s);
+    if (vis <= now) {
+      best = v;
+      *slot = s;
+    }
+  }
+  return best;
+}
+
+// Slice i has work unless its last update is idempotent: it used the same
+// predecessor version for F and G (vF == vG) and no newer version is
+// visible.  In paper-literal mode it always has work.
+__device__ bool has_work(const AsyncDev& a, int i, unsigned long long now) {
+  if (ld_acquire(a.kcount + i - 1) == 0 || a.paper_literal) return true;
+  if (!ld_acquire(a.lastfg + i - 1)) return true;
+  if (i == 1) return false;  // lam_0 = u0 never changes
+  int slot = -1;
+  return freshest_visible(a, i - 1, now, &slot) > ld_acquire(a.xver + i - 1);
+}
+
+// Stop test of the monitor (any team leader may evaluate it), scanning the
+// slices in order.  Slice i is "settled" when its last update was idempotent
+// (vF == vG == the predecessor's latest version): it cannot change again
+// unless its predecessor does, and by induction along the scan a settled
+// prefix stays settled.  Quiescence = every slice settled (then
+// lam_i = F(lam_{i-1}) for all i).  Tolerance rule (Eq. (22) read per
+// slice): every slice has updated and is settled or had a last increment
+// below tol.
+__device__ bool stop_condition(const AsyncDev& a) {
+  bool quiet = true;
+  bool below = !a.quiescence;
+  for (int i = 1; i <= a.N; ++i) {
+    const int k = ld_acquire(a.kcount + i - 1);
+    if (k < 1) return false;
+    const int pred_latest = i == 1 ? 0 : ld_acquire(a.latest + i - 1);
+    const bool settled = !a.paper_literal && ld_acquire(a.lastfg + i - 1) &&
+                         ld_acquire(a.xver + i - 1) == pred_latest;
+    if (!settled) quiet = false;
+    if (below && !settled) {
+      const double d = __ldcg(a.delta + i - 1);
+      if (!(d < a.tol)) below = false;
+    }
+    if (!quiet && !below) return false;
+  }
+  return quiet || below;
+}
+
+__device__ void set_status(const AsyncDev& a, int st) {
+  atomicCAS(a.status, AST_OK, st);
+  atomicExch(a.stop, 1);
+}
+
+// Fine propagation v = F(xs_i) by the team: f_steps explicit steps, one team
+// barrier after each.  FP64 steps ping-pong through the CG r/p vectors; FP32
+// steps through the same memory viewed as floats.
+template <typename T>
+__device__ bool team_fine(const AsyncDev& a, const TeamBarrier& bar, const double* xs, double* v,
+                          double* pp0, double* pp1, int tb) {
+  const long long M = a.g.M;
+  const long long t0 = tb * (long long)blockDim.x + threadIdx.x;
+  const long long nt = (long long)a.C * blockDim.x;
+  const T c0 = T(a.fst.c0), rx = T(a.fst.rx), ry = T(a.fst.ry), rz = T(a.fst.rz);
+  StencilVar<T> cv;
+  if constexpr (sizeof(T) == 8) {
+    cv = a.fv;
+  } else {
+    cv = a.fv32;
+  }
+  T* buf0 = reinterpret_cast<T*>(pp0);
+  T* buf1 = reinterpret_cast<T*>(pp1);
+  const int S = a.f_steps;
+  if (S == 1) {
+    for (long long i = t0; i < M; i += nt)
+      v[i] = double(fstep_at<T, double>(a.g, c0, rx, ry, rz, a.var, cv, xs, i));
+    return bar.sync();
+  }
+  for (long long i = t0; i < M; i += nt) buf0[i] = fstep_at<T, double>(a.g, c0, rx, ry, rz, a.var, cv, xs, i);
+  if (!bar.sync()) return false;
+  const T* src = buf0;
+  for (int s = 1; s < S - 1; ++s) {
+    T* dst = (src == buf0) ? buf1 : buf0;
+    for (long long i = t0; i < M; i += nt) dst[i] = fstep_at<T, T>(a.g, c0, rx, ry, rz, a.var, cv, src, i);
+    if (!bar.sync()) return false;
+    src = dst;
+  }
+  for (long long i = t0; i < M; i += nt)
+    v[i] = double(fstep_at<T, T>(a.g, c0, rx, ry, rz, a.var, cv, src, i));
+  return bar.sync();
+}
+
+__global__ void __launch_bounds__(ATHREADS) async_kernel(AsyncDev a) {
+  const int team = blockIdx.x / a.C;
+  const int tb = blockIdx.x % a.C;
+  const bool leader = tb == 0 && threadIdx.x == 0;
+  const long long M = a.g.M;
+  const long long t0 = tb * (long long)blockDim.x + threadIdx.x;
+  const long long nt = (long long)a.C * blockDim.x;
+  const unsigned long long deadline = globaltimer() + a.timeout_ns;
+  // barrier waits get a grace period beyond the run limit so that a normal
+  // stop at the limit is not reported as a barrier failure
+  TeamBarrier bar{a.bar + 2 * team, a.bar + 2 * team + 1, a.C, deadline + 2000000000ull,
+                  a.barrier_err};
+  int* ctrl = a.ctrl + 8 * team;
+  double* tv = a.tv + (long long)team * M;
+  double* cgx = a.tcg + (long long)team * 4 * M;
+  CgWork ws{cgx, cgx + M, cgx + 2 * M, cgx + 3 * M, a.tpart + (long long)team * 6 * a.C};
+  int cursor = 0;                        // round-robin over owned slices (leader only)
+  const int n_own = team < a.N ? (a.N - 1 - team) / a.T + 1 : 0;
+  // Decision words alternate between two slots: after an IDLE decision the
+  // leader writes the next decision while a slower block of the team may still
+  // be reading the previous one, so consecutive decisions must not share words.
+  unsigned dnum = 0;
+
+  while (true) {
+    int* dslot = ctrl + 2 * (dnum++ & 1u);
+    // ---------------- decision (leader) ----------------
+    if (leader) {
+      int dec = DEC_IDLE, slice = 0;
+      const unsigned long long now = globaltimer();
+      if (now > deadline) set_status(a, AST_TIMEOUT);
+      if (ld_acquire(a.stop) || ld_acquire(a.barrier_err)) {
+        dec = DEC_STOP;
+      } else {
+        for (int c = 0; c < n_own; ++c) {
+          const int i = team + 1 + ((cursor + c) % n_own) * a.T;
+          if (has_work(a, i, now)) {
+            dec = DEC_UPDATE;
+            slice = i;
+            cursor = (cursor + c + 1) % n_own;
+            break;
+          }
+        }
+        if (dec == DEC_IDLE) {
+          if (stop_condition(a)) {
+            atomicExch(a.stop, 1);
+            dec = DEC_STOP;
+          } else {
+            __nanosleep(2000);
+          }
+        }
+      }
+      dslot[0] = dec;
+      dslot[1] = slice;
+    }
+    if (!bar.sync()) break;
+    const int dec = __ldcg(dslot);
+    if (dec == DEC_STOP) break;
+    if (dec == DEC_IDLE) continue;
+    const int i = __ldcg(dslot + 1);
+    double* xs = a.xs + slice_off(a, i);
+    double* w = a.w + slice_off(a, i);
+    const int vF = ld_acquire(a.xver + i - 1);
+    const int k = ld_acquire(a.kcount + i - 1);
+    unsigned long long t_start = 0;
+    if (leader) t_start = globaltimer();
+
+    // ---------------- fine propagation v = F(xs_i) ----------------
+    const bool ok = a.f_prec == 32 ? team_fine<float>(a, bar, xs, tv, ws.r, ws.p, tb)
+                                   : team_fine<double>(a, bar, xs, tv, ws.r, ws.p, tb);
+    if (!ok) break;
+
+    // ---------------- freshest visible predecessor version ----------------
+    int vG = vF;
+    for (int attempt = 0;; ++attempt) {
+      if (leader) {
+        int slot = -1, cand = -1;
+        if (i > 1) cand = freshest_visible(a, i - 1, globaltimer(), &slot);
+        ctrl[4] = cand > vF ? cand : vF;
+        ctrl[5] = cand > vF ? slot : -1;
+      }
+      if (!bar.sync()) return;
+      vG = __ldcg(ctrl + 4);
+      const int slot = __ldcg(ctrl + 5);
+      if (vG == vF) break;
+      const double* src = ring_slot(a, i - 1, slot);
+      for (long long p = t0; p < M; p += nt) xs[p] = __ldcg(src + p);
+      __threadfence();
+      if (!bar.sync()) return;
+      if (leader) ctrl[6] = ld_acquire(a.ring_ver + (i - 2) * RING + slot) == vG ? 1 : 0;
+      if (!bar.sync()) return;
+      if (__ldcg(ctrl + 6)) break;   // copy consistent (seqlock check passed)
+      if (attempt > 1000) {
+        if (leader) set_status(a, AST_BARRIER);
+        return;
+      }
+    }
+
+    // ---------------- coarse solve w_new = G(xs_i) ----------------
+    const double* wn = w;
+    int cg_it = 0;
+    if (vG > vF) {
+      cg_it = cg_core(a.g, a.gst, a.var, a.gv, xs, w, a.rtol, a.maxit, ws, bar, a.C, tb, nullptr);
+      if (cg_it < 0) break;
+      wn = ws.x;
+    }
+
+    // ---------------- correction, increment, publish ----------------
+    const int s_new = (k + 1) % RING, s_cur = k % RING;
+    if (leader) {
+      atomicExch(a.ring_ver + (i - 1) * RING + s_new, -1);  // seqlock: slot being written
+      a.tdelta[team] = 0ull;
+      __threadfence();
+    }
+    if (!bar.sync()) break;
+    {
+      double* dst = ring_slot(a, i, s_new);
+      const double* cur = ring_slot(a, i, s_cur);
+      unsigned long long dmax = 0ull;
+      for (long long p = t0; p < M; p += nt) {
+        const double wo = w[p];
+        const double x = wn[p];
+        const double ln = __dsub_rn(__dadd_rn(x, tv[p]), wo);
+        const unsigned long long d = abs_bits(__dsub_rn(ln, cur[p]));
+        dmax = d > dmax ? d : dmax;
+        dst[p] = ln;
+        if (wn != w) w[p] = x;
+      }
+      dmax = warp_max_u64(dmax);
+      if ((threadIdx.x & 31) == 0 && dmax) atomicMax(a.tdelta + team, dmax);
+      __threadfence();
+    }
+    if (!bar.sync()) break;
+    if (leader) {
+      const unsigned long long now = globaltimer();
+      unsigned long long vis = now;
+      if (a.delays && a.delay_cols > 0)
+        vis += (unsigned long long)(a.delays[(long long)(i - 1) * a.delay_cols + (k % a.delay_cols)] *
+                                    a.delay_unit_ns);
+      const unsigned long long dbits = atomicAdd(a.tdelta + team, 0ull);
+      double dl;
+      memcpy(&dl, &dbits, sizeof dl);
+      st_release_u64(a.ring_vis + (i - 1) * RING + s_new, vis);
+      st_release(a.ring_ver + (i - 1) * RING + s_new, k + 1);
+      st_release(a.latest + i, k + 1);
+      __stcg(a.delta + i - 1, dl);
+      st_release(a.xver + i - 1, vG);
+      st_release(a.lastfg + i - 1, vG == vF ? 1 : 0);
+      __threadfence();
+      st_release(a.kcount + i - 1, k + 1);
+      const unsigned long long idx = atomicAdd(a.log_count, 1ull);
+      if ((long long)idx < a.log_cap) {
+        pr_event e;
+        e.slice = i;
+        e.version = k + 1;
+        e.vF = vF;
+        e.vG = vG;
+        e.cg_iters = cg_it;
+        e.team = team;
+        e.delta = dl;
+        e.t_start = t_start;
+        e.t_end = vis;
+        a.log[idx] = e;
+      } else {
+        set_status(a, AST_LOGFULL);
+      }
+      if (stop_condition(a)) atomicExch(a.stop, 1);
+    }
+  }
+}
+
+__global__ void async_init(AsyncDev a) {
+  const long long M = a.g.M;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)a.N * RING;
+       t += (long long)gridDim.x * blockDim.x) {
+    a.ring_ver[t] = (t % RING) == 0 ? 0 : -1;
+    a.ring_vis[t] = 0ull;
+  }
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t <= a.N;
+       t += (long long)gridDim.x * blockDim.x) {
+    a.latest[t] = 0;
+    if (t < a.N) {
+      a.xver[t] = 0;
+      a.kcount[t] = 0;
+      a.delta[t] = __longlong_as_double(0x7ff0000000000000LL);  // +inf
+      a.lastfg[t] = 0;
+    }
+  }
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < 2LL * a.T;
+       t += (long long)gridDim.x * blockDim.x)
+    a.bar[t] = 0u;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < 8LL * a.T;
+       t += (long long)gridDim.x * blockDim.x)
+    a.ctrl[t] = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *a.stop = 0;
+    *a.status = 0;
+    *a.barrier_err = 0;
+    *a.log_count = 0ull;
+  }
+  (void)M;
+}
+
+// lam_out row i <- slice i's latest version (row 0 = u0 already there).
+__global__ void async_gather(AsyncDev a, double* lam) {
+  const long long M = a.g.M;
+  for (int i = 1 + blockIdx.y; i <= a.N; i += gridDim.y) {
+    const int k = a.kcount[i - 1];
+    const double* src = ring_slot(a, i, k % RING);
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < M;
+         p += (long long)gridDim.x * blockDim.x)
+      lam[(long long)i * M + p] = src[p];
+  }
+}
+
+int async_max_blocks_per_sm() {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, async_kernel, ATHREADS, 0) !=
+          cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  return per_sm;
+}
+
+}  // namespace
+
+int run_async(pr_ctx* c, const pr_async_opts* o, double* lam, pr_stats* st, pr_event* log_host,
+              size_t log_cap, size_t* log_len) {
+  const pr_problem& p = c->prob;
+  if (p.f_scheme != PR_EXPLICIT_EULER || p.g_solver != PR_SOLVER_CG)
+    return fail(c, PR_EINVAL, "asynchronous path needs the explicit fine scheme and the CG coarse solver");
+  if (o->timeout_s <= 0.0) return fail(c, PR_EINVAL, "timeout_s must be > 0");
+  if (o->delays_dev && o->delay_cols <= 0) return fail(c, PR_EINVAL, "delay_cols must be > 0");
+  const long long M = c->g.M;
+  const int N = p.N;
+  const int capacity = c->num_sms * async_max_blocks_per_sm();
+  int C = o->ctas_per_slice > 0 ? o->ctas_per_slice : std::max(1, std::min(8, capacity / N));
+  if (C > capacity) C = capacity;
+  int T = std::min(N, capacity / C);
+  if (T < 1) return fail(c, PR_EINVAL, "ctas_per_slice exceeds the co-resident capacity");
+
+  // workspace layout (doubles first, then 8-byte scalars, then ints)
+  const size_t d_ring = (size_t)N * RING * M, d_xs = (size_t)N * M, d_tv = (size_t)T * M,
+               d_tcg = (size_t)T * 4 * M, d_tpart = (size_t)T * 6 * C, d_delta = N;
+  const size_t n_dbl = d_ring + d_xs + d_tv + d_tcg + d_tpart + d_delta;
+  const size_t n_u64 = (size_t)N * RING + T + 1 + (log_cap ? 0 : 0);
+  const size_t n_int = (size_t)N * RING + (N + 1) + 4 * (size_t)N + 2 * (size_t)T + 8 * (size_t)T + 3;
+  const size_t bytes = n_dbl * 8 + n_u64 * 8 + n_int * 4 + 256;
+  if (c->async_ws_bytes < bytes) {
+    if (c->async_ws) cudaFree(c->async_ws);
+    c->async_ws = nullptr;
+    c->async_ws_bytes = 0;
+    PR_CUDA(c, cudaMalloc(&c->async_ws, bytes));
+    c->async_ws_bytes = bytes;
+  }
+  pr_event* dlog = nullptr;
+  if (log_cap) PR_CUDA(c, cudaMalloc(&dlog, log_cap * sizeof(pr_event)));
+
+  AsyncDev a{};
+  a.g = c->g;
+  a.N = N;
+  a.T = T;
+  a.C = C;
+  a.f_steps = p.f_steps;
+  a.f_prec = p.f_prec;
+  a.var = c->var_kappa;
+  a.fst = c->fst;
+  a.gst = c->gst;
+  a.fv = c->fvar;
+  a.gv = c->gvar;
+  a.fv32 = c->fvar32;
+  a.rtol = p.g_rtol;
+  a.tol = p.tol;
+  a.maxit = p.g_maxit;
+  a.paper_literal = o->paper_literal;
+  a.quiescence = o->quiescence;
+  a.u0 = p.u0_dev;
+  double* dp = static_cast<double*>(c->async_ws);
+  a.ring = dp;
+  dp += d_ring;
+  a.xs = dp;
+  dp += d_xs;
+  a.tv = dp;
+  dp += d_tv;
+  a.tcg = dp;
+  dp += d_tcg;
+  a.tpart = dp;
+  dp += d_tpart;
+  a.delta = dp;
+  dp += d_delta;
+  unsigned long long* up = reinterpret_cast<unsigned long long*>(dp);
+  a.ring_vis = up;
+  up += (size_t)N * RING;
+  a.tdelta = up;
+  up += T;
+  a.log_count = up;
+  up += 1;
+  int* ip = reinterpret_cast<int*>(up);
+  a.ring_ver = ip;
+  ip += (size_t)N * RING;
+  a.latest = ip;
+  ip += N + 1;
+  a.xver = ip;
+  ip += N;
+  a.kcount = ip;
+  ip += N;
+  a.lastfg = ip;
+  ip += N;
+  ip += N;  // reserved
+  a.bar = reinterpret_cast<unsigned*>(ip);
+  ip += 2 * T;
+  a.ctrl = ip;
+  ip += 8 * T;
+  a.stop = ip++;
+  a.status = ip++;
+  a.barrier_err = ip++;
+  a.w = c->w;
+  a.log = dlog;
+  a.log_cap = (long long)log_cap;
+  a.delays = o->delays_dev;
+  a.delay_cols = o->delay_cols;
+  a.delay_unit_ns = o->delay_unit_ns;
+
+  PR_CUDA(c, cudaEventRecord(c->ev[0], c->stream));
+  // predictor (Algorithm 2, first lines): lam_i^0 = w_i^0 = G(lam_{i-1}^0)
+  PR_CUDA(c, cudaMemcpyAsync(lam, p.u0_dev, M * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  long long launches = 0, cg_total = 0;
+  for (int i = 1; i <= N; ++i) {
+    CgArgs g{};
+    g.b = lam + (size_t)(i - 1) * M;
+    g.x0 = g.b;
+    g.out = c->w + (size_t)(i - 1) * M;
+    g.lam = lam + (size_t)i * M;
+    g.iters = c->cg_iters_dev + i;
+    g.mode = CG_PREDICTOR;
+    PR_CUDA(c, cg_solve(c, g));
+    ++launches;
+  }
+  // version 0 of every slice, snapshots xs_i = lam_{i-1}^0
+  async_init<<<64, 256, 0, c->stream>>>(a);
+  ++launches;
+  PR_CUDA(c, cudaMemcpy2DAsync(a.ring, RING * M * sizeof(double), lam + M, M * sizeof(double),
+                               M * sizeof(double), N, cudaMemcpyDeviceToDevice, c->stream));
+  PR_CUDA(c, cudaMemcpyAsync(a.xs, lam, (size_t)N * M * sizeof(double), cudaMemcpyDeviceToDevice,
+                             c->stream));
+  std::vector<int> pit(N + 1);
+  PR_CUDA(c, cudaMemcpyAsync(pit.data(), c->cg_iters_dev, (N + 1) * sizeof(int),
+                             cudaMemcpyDeviceToHost, c->stream));
+  PR_CUDA(c, cudaStreamSynchronize(c->stream));
+  for (int i = 1; i <= N; ++i) cg_total += pit[i];
+
+  a.timeout_ns = (unsigned long long)(o->timeout_s * 1e9);
+
+  // the persistent kernel: all T*C blocks co-resident (cooperative launch)
+  PR_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
+  void* args[] = {&a};
+  cudaError_t e = cudaLaunchCooperativeKernel((void*)async_kernel, dim3(T * C), dim3(ATHREADS), args,
+                                              0, c->stream);
+  if (e != cudaSuccess) {
+    if (dlog) cudaFree(dlog);
+    return cuda_fail(c, e, "async kernel launch");
+  }
+  ++launches;
+  PR_CUDA(c, cudaEventRecord(c->ev[2], c->stream));
+  async_gather<<<dim3(64, std::min(N, 64)), 256, 0, c->stream>>>(a, lam);
+  ++launches;
+  PR_CUDA(c, cudaEventRecord(c->ev[3], c->stream));
+  int flags[3] = {0, 0, 0};
+  unsigned long long nlog = 0;
+  std::vector<int> kc(N);
+  std::vector<double> dl(N);
+  PR_CUDA(c, cudaMemcpyAsync(flags, a.stop, 3 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  PR_CUDA(c, cudaMemcpyAsync(&nlog, a.log_count, sizeof nlog, cudaMemcpyDeviceToHost, c->stream));
+  PR_CUDA(c, cudaMemcpyAsync(kc.data(), a.kcount, N * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  PR_CUDA(c, cudaMemcpyAsync(dl.data(), a.delta, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  PR_CUDA(c, cudaStreamSynchronize(c->stream));
+  const size_t nkeep = std::min<size_t>((size_t)nlog, log_cap);
+  std::vector<pr_event> ev(nkeep);
+  if (nkeep) {
+    PR_CUDA(c, cudaMemcpy(ev.data(), dlog, nkeep * sizeof(pr_event), cudaMemcpyDeviceToHost));
+    if (log_host) memcpy(log_host, ev.data(), nkeep * sizeof(pr_event));
+  }
+  if (dlog) cudaFree(dlog);
+  if (log_len) *log_len = nkeep;
+  for (const pr_event& x : ev) cg_total += x.cg_iters;
+  float t_all = 0, t_kernel = 0;
+  cudaEventElapsedTime(&t_all, c->ev[0], c->ev[3]);
+  cudaEventElapsedTime(&t_kernel, c->ev[1], c->ev[2]);
+  int kmax = 0;
+  double dmax = 0.0;
+  for (int i = 0; i < N; ++i) {
+    c->last_k[i] = kc[i];
+    c->last_delta[i] = dl[i];
+    kmax = std::max(kmax, kc[i]);
+    dmax = std::max(dmax, dl[i]);
+  }
+  pr_stats S{};
+  S.iterations = kmax;
+  S.max_delta = dmax;
+  S.events = (long long)nlog;
+  long long ups = 0;
+  for (int i = 0; i < N; ++i) ups += kc[i];
+  S.fine_lups = ups * M * p.f_steps;
+  S.cg_iterations = cg_total;
+  S.t_total_ms = t_all;
+  S.t_fine_ms = 0;
+  S.t_coarse_ms = 0;
+  S.launches = launches;
+  const int status = flags[1], berr = flags[2];
+  S.converged = (status == AST_OK && !berr) ? 1 : 0;
+  if (st) *st = S;
+  if (berr || status == AST_BARRIER) return fail(c, PR_ETIMEOUT, "async: a bounded barrier wait expired");
+  if (status == AST_TIMEOUT) return fail(c, PR_ETIMEOUT, "async: wall-clock limit reached");
+  if (status == AST_LOGFULL) return fail(c, PR_ELOGFULL, "async: event log capacity exceeded");
+  (void)t_kernel;
+  return PR_OK;
 }
 
 }  // namespace pr

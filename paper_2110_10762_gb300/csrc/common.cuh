@@ -117,6 +117,9 @@ int cuda_fail(pr_ctx* c, cudaError_t e, const char* where);
 cudaError_t explicit_fine(pr_ctx* c, const double* in, double* out, int count, int steps,
                           int prec);
 cudaError_t build_var_coefficients(pr_ctx* c);
+// One FP64 explicit step u' = S u on `count` states (S is symmetric, so this is
+// also the transposed step used by the adjoint).
+cudaError_t explicit_step64(pr_ctx* c, const double* in, double* out, int count);
 
 // ---- tridiagonal partition solver (tridiag.cu)
 cudaError_t tri_build(pr_ctx* c, TriTables* t, int n, double r, const double* kappa);

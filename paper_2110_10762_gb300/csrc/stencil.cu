@@ -264,6 +264,11 @@ cudaError_t build_var_coefficients(pr_ctx* c) {
   return cudaGetLastError();
 }
 
+cudaError_t explicit_step64(pr_ctx* c, const double* in, double* out, int count) {
+  if (count <= 0) return cudaSuccess;
+  return launch_step<double, double, double>(c, in, out, count, c->fvar);
+}
+
 cudaError_t explicit_fine(pr_ctx* c, const double* in, double* out, int count, int steps,
                           int prec) {
   if (count <= 0 || steps <= 0) return cudaSuccess;
