@@ -34,11 +34,25 @@ WORKLOADS = {
                        "G=1 implicit Euler step by CG (rtol 1e-10), FP64, sync Parareal, tol 1e-10",
     "heat3d_mixed": "3D heat 256^3, N=128 slices, F=64 explicit 7-pt steps (dt=0.15h^2), "
                     "G=implicit Euler by CG (rtol 1e-10), FP32 fine / FP64 coarse, sync, tol 1e-5",
+    "heat1d_thomas": "1D heat 1023 pts, N=16 slices, F=100 implicit Euler steps, G=1 step, both "
+                     "by the batched partition Thomas/PCR solver, FP64, sync, tol 1e-10",
+    "heat2d_async": "the 2D heat 1024x1024 N=64 FP64 problem solved by the asynchronous persistent "
+                    "kernel (no injected delays) next to the synchronous solve, tol 1e-10",
+    "heat3d_varkappa_async": "3D variable-kappa heat 192^3, N=256, F=32 explicit 7-pt steps, FP32 "
+                             "fine / FP64 coarse, async with seeded publish delays 0-4 fine-step "
+                             "units vs sync, tol 1e-5",
+    "heat2d_inverse": "2D inverse heat 512x512, variable kappa, N=32, F=128, K=6 Parareal "
+                      "iterations: loss + discrete-adjoint gradient wrt u0 and kappa, FP64",
 }
-# FP64-pipe operations per fine cell update of the explicit step (DADD/DMUL/DFMA
-# each one issue slot): 2D 5-point = 2 DADD + 1 DMUL + 2 DFMA; 3D 7-point = 3 + 1 + 3.
-FP64_OPS_PER_LUP = {2: 5, 3: 7}
+# FP64-pipe operations per fine cell update (DADD/DMUL/DFMA each one issue slot):
+# 2D 5-point = 2 DADD + 1 DMUL + 2 DFMA; 3D 7-point = 3 + 1 + 3; 1D implicit step by the
+# partition solver = 2 (forward) + 1 (back) + 2 (rebuild) per unknown.
+FP64_OPS_PER_LUP = {1: 5, 2: 5, 3: 7}
 NOMINAL_FP64_OPS = 625.0  # G FP64-pipe ops/s: 1.25 TFLOP/s nominal / 2 flops per DFMA
+# DRAM bytes (read + write) per cell update of the dominant kernel, from one ncu capture
+# of the unchanged kernel (profiles/step2d_fp64_heat2d_1024x1024.md: 1017.0 MB for
+# 63 x 1048576 updates); None where no capture of the current kernel exists.
+NCU_TRAFFIC_PER_LUP = {"heat2d_explicit": 1017.0e6 / (63 * 1048576)}
 
 
 def parse():
@@ -50,6 +64,8 @@ def parse():
     ap.add_argument("--workload", default="heat2d_explicit", choices=list(WORKLOADS))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
+    ap.add_argument("--profile", action="store_true",
+                    help="run exactly one solve and nothing else (for ncu launch lists)")
     return ap.parse_args()
 
 
@@ -119,6 +135,20 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def replica_aggregate(units, seconds, world, device="cpu"):
+    """Whole-job throughput of independent replicas: (sum of units over ranks) /
+    (max time over ranks).  Returns (units per second, max seconds)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+        u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        seconds, units = float(t.item()), float(u.item())
+    return units / seconds, seconds
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -128,8 +158,20 @@ def dist_setup(args):
 
 def problem_of(name):
     from synthetic import preset
-    p = preset(name, "full")
-    return p
+    base = {"heat2d_async": "heat2d_explicit"}.get(name, name)
+    return preset(base, "full")
+
+
+def problem_struct(pr, p, u0, kappa=None, **over):
+    """pr_problem for a preset dict (T0 = 0, T = N * f_steps * dt)."""
+    kw = dict(dim=p["dim"], n=p["n"], T0=0.0, T=p["N"] * p["f_steps"] * p["dt"], N=p["N"],
+              u0=u0, kappa=kappa,
+              f_scheme=pr.PR_IMPLICIT_EULER if p.get("f_scheme") == "implicit" else pr.PR_EXPLICIT_EULER,
+              f_steps=p["f_steps"], f_prec=p.get("f_prec", 64),
+              g_solver=pr.PR_SOLVER_THOMAS if p.get("g_solver") == "thomas" else pr.PR_SOLVER_CG,
+              g_rtol=p.get("g_rtol", 1e-10), tol=p.get("tol", 0.0))
+    kw.update(over)
+    return pr.make_problem(**kw)
 
 
 def cpu_sample(p, slices=2, steps=None):
@@ -174,6 +216,181 @@ def run_reference(args, world, rank):
     return 0
 
 
+def mixed_vs_fp64(pr, torch, p, u0, lam_mixed, t_mixed_ms, args, local):
+    """The same solve with FP64 fine steps, and the accuracy of both against the
+    FP64 serial fine solution: err = max_i ||lam_i - lam*_i||_inf / max_i ||lam*_i||_inf."""
+    N, M = p["N"], u0.numel()
+    ctx = pr.parareal_create(local, torch.cuda.current_stream())
+    try:
+        prob = problem_struct(pr, p, u0, None, f_prec=64)
+        pr.parareal_set_problem(ctx, prob)
+        lam64 = torch.empty_like(lam_mixed)
+        for _ in range(max(1, min(args.warmup, 1))):
+            pr.parareal_run_sync(ctx, lam64)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k64 = 0
+        ev0.record()
+        for _ in range(args.steps):
+            _, st = pr.parareal_run_sync(ctx, lam64)
+            k64 = st.iterations
+        ev1.record()
+        torch.cuda.synchronize()
+        t64 = ev0.elapsed_time(ev1) / args.steps
+        star = torch.empty_like(lam_mixed)
+        sst = pr.parareal_serial_fine(ctx, star)
+        scale = star.abs().max().item()
+        err_m = (lam_mixed - star).abs().max().item() / scale
+        err_64 = (lam64 - star).abs().max().item() / scale
+        return {"t_mixed_ms": t_mixed_ms, "t_fp64_ms": t64, "speedup": t64 / t_mixed_ms,
+                "err_mixed": err_m, "err_fp64": err_64, "k_fp64": k64,
+                "serial_fine_fp64_ms": sst.t_total_ms,
+                "accuracy_target": 1e-5, "mixed_meets_target": err_m <= 1e-5}
+    finally:
+        pr.parareal_destroy(ctx)
+
+
+def _timed(torch, fn, steps):
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res = []
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(steps):
+        res.append(fn())
+    ev1.record()
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1) / steps, res
+
+
+def run_async_workload(args, local):
+    """Asynchronous persistent kernel vs the synchronous driver on one problem."""
+    import numpy as np
+    import torch
+
+    import paper_2110_10762_gb300 as pr
+    from synthetic import delay_table
+
+    torch.cuda.set_device(local)
+    p = problem_of(args.workload)
+    N, M = p["N"], int(np.prod(p["n"]))
+    u0 = torch.from_numpy(p["u0"].reshape(-1).copy()).cuda()
+    kappa = (torch.from_numpy(p["kappa"].reshape(-1).copy()).cuda()
+             if p.get("kappa") is not None else None)
+    ctx = pr.parareal_create(local, torch.cuda.current_stream())
+    pr.parareal_set_problem(ctx, problem_struct(pr, p, u0, kappa))
+    lam = torch.empty((N + 1) * M, dtype=torch.float64, device="cuda")
+    delays, unit_ns = None, 0.0
+    if "delay_seed" in p:
+        # one delay unit = the measured duration of one fine step of one slice
+        x = lam[:M].clone()
+        y = torch.empty_like(x)
+        pr.parareal_fine(ctx, x, y, 1)
+        t_ms, _ = _timed(torch, lambda: pr.parareal_fine(ctx, x, y, 1), 3)
+        unit_ns = t_ms * 1e6 / p["f_steps"]
+        delays = torch.from_numpy(delay_table(N, 64, seed=p["delay_seed"])).cuda()
+    opts = pr.make_async_opts(timeout_s=300.0, delays=delays, delay_unit_ns=unit_ns)
+    for _ in range(args.warmup):
+        pr.parareal_run_async(ctx, opts, lam, log_cap=1 << 20)
+    with Clocks(local) as clk:
+        t_async, res = _timed(torch, lambda: pr.parareal_run_async(ctx, opts, lam, log_cap=1 << 20),
+                              args.steps)
+    code, st, log = res[-1]
+    lam_async = lam.clone()
+    for _ in range(min(args.warmup, 1)):
+        pr.parareal_run_sync(ctx, lam)
+    t_sync, sres = _timed(torch, lambda: pr.parareal_run_sync(ctx, lam), args.steps)
+    sst = sres[-1][1]
+    # accuracy of both against the FP64 serial fine solution
+    ctx64 = pr.parareal_create(local, torch.cuda.current_stream())
+    pr.parareal_set_problem(ctx64, problem_struct(pr, p, u0, kappa, f_prec=64))
+    star = torch.empty_like(lam)
+    pr.parareal_serial_fine(ctx64, star)
+    pr.parareal_destroy(ctx64)
+    scale = star.abs().max().item()
+    lups = sum(r[1].fine_lups for r in res)
+    value = lups / (t_async * args.steps / 1e3) / 1e9
+    cg_ops = {2: 10.3, 3: 12.3}[p["dim"]]
+    fp64_ops = st.cg_iterations * M * cg_ops + (
+        st.fine_lups * FP64_OPS_PER_LUP[p["dim"]] if p.get("f_prec", 64) == 64 else 0)
+    roof = {"bound": "alu", "kernel": "async_kernel", "unit": "Gop/s",
+            "achieved": fp64_ops / (t_async / 1e3) / 1e9, "peak": NOMINAL_FP64_OPS,
+            "peak_kind": "nominal FP64 pipe", "traffic": None,
+            "note": "FP64-pipe work of the CG solves"
+                    + (" and FP64 fine steps" if p.get("f_prec", 64) == 64 else "")
+                    + " over the whole async run (predictor included)"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    out = {"metric": "fine GLUP/s", "value": value, "unit": "GLUP/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_async,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32/f64" if p.get("f_prec", 64) == 32 else "f64", "data": "synthetic",
+           "config": {"workload": WORKLOADS[args.workload], "grid": list(p["n"]), "N": N,
+                      "f_steps": p["f_steps"], "tol": p["tol"],
+                      "delay_unit_ns": unit_ns, "delays": delays is not None},
+           "async": {"status": int(code), "time_to_tol_ms": t_async, "kappa": st.iterations,
+                     "events": st.events, "cg_iterations": st.cg_iterations,
+                     "err_vs_serial_fine": (lam_async - star).abs().max().item() / scale},
+           "sync": {"time_to_tol_ms": t_sync, "k": sst.iterations,
+                    "cg_iterations": sst.cg_iterations,
+                    "err_vs_serial_fine": (lam - star).abs().max().item() / scale},
+           "async_speedup_vs_sync": t_sync / t_async,
+           "kappa_over_k": st.iterations / max(sst.iterations, 1),
+           "roofline": roof, "gpu_launches": st.launches, "clocks": clk.summary()}
+    pr.parareal_destroy(ctx)
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_adjoint_workload(args, local):
+    """Loss and discrete-adjoint gradient through K sync iterations (ParaRealFn)."""
+    import numpy as np
+    import torch
+
+    import paper_2110_10762_gb300 as pr
+    from paper_2110_10762_gb300.autograd import ParaRealFn
+
+    torch.cuda.set_device(local)
+    p = problem_of(args.workload)
+    N, M, K, nf = p["N"], int(np.prod(p["n"])), p["K"], p["f_steps"]
+    T = N * nf * p["dt"]
+    u0 = torch.from_numpy(p["u0"].reshape(-1).copy()).cuda()
+    kap = torch.from_numpy(p["kappa"].reshape(-1).copy()).cuda()
+    kstar = torch.from_numpy(p["kappa_star"].reshape(-1).copy()).cuda()
+    ctx = pr.parareal_create(local, torch.cuda.current_stream())
+    pr.parareal_set_problem(ctx, problem_struct(pr, p, u0, kstar))
+    obs = torch.empty((N + 1) * M, dtype=torch.float64, device="cuda")
+    pr.parareal_serial_fine(ctx, obs)
+    pr.parareal_destroy(ctx)
+    u_obs = obs[N * M:].clone()
+    del obs
+    spec = dict(dim=p["dim"], n=p["n"], T=T, N=N, f_steps=nf, K=K, g_rtol=p["g_rtol"])
+
+    def step():
+        a = u0.clone().requires_grad_(True)
+        b = kap.clone().requires_grad_(True)
+        out = ParaRealFn.apply(a, b, spec)
+        loss = 0.5 * ((out - u_obs) ** 2).sum()
+        loss.backward()
+        return loss.item(), a.grad, b.grad
+
+    for _ in range(args.warmup):
+        step()
+    with Clocks(local) as clk:
+        t_ms, res = _timed(torch, step, args.steps)
+    loss, gu, gk = res[-1]
+    fwd = sum(N - k for k in range(K)) * M * nf
+    # forward + recomputed fine states (n_f - 1 per slice) + transposed steps (n_f per slice)
+    lups = fwd + sum(N - k for k in range(K)) * M * (2 * nf - 1)
+    out = {"metric": "fine GLUP/s", "value": lups / (t_ms / 1e3) / 1e9, "unit": "GLUP/s",
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": WORKLOADS[args.workload], "grid": list(p["n"]), "N": N,
+                      "f_steps": nf, "K": K},
+           "loss": loss, "grad_u0_norm": gu.norm().item(), "grad_kappa_norm": gk.norm().item(),
+           "gradients_per_s": 1e3 / t_ms, "clocks": clk.summary()}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -191,12 +408,19 @@ def run_ours(args, world, rank, local):
     N = p["N"]
     stream = torch.cuda.current_stream()
     u0 = torch.from_numpy(p["u0"].reshape(-1).copy()).cuda()
+    kappa = (torch.from_numpy(p["kappa"].reshape(-1).copy()).cuda()
+             if p.get("kappa") is not None else None)
     ctx = pr.parareal_create(local, stream)
-    prob = pr.make_problem(dim=dim, n=p["n"], T0=0.0, T=N * p["f_steps"] * p["dt"], N=N, u0=u0,
-                           f_steps=p["f_steps"], f_prec=p.get("f_prec", 64),
-                           g_rtol=p["g_rtol"], tol=p["tol"])
+    prob = problem_struct(pr, p, u0, kappa)
     pr.parareal_set_problem(ctx, prob)
     lam = torch.empty((N + 1) * M, dtype=torch.float64, device="cuda")
+    if args.profile:
+        code, st = pr.parareal_run_sync(ctx, lam)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": args.workload, "iterations": st.iterations,
+                          "launches": st.launches, "t_total_ms": st.t_total_ms}), flush=True)
+        pr.parareal_destroy(ctx)
+        return 0
 
     def barrier():
         if world > 1:
@@ -217,17 +441,15 @@ def run_ours(args, world, rank, local):
         ev1.record(stream)
         torch.cuda.synchronize()
     barrier()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     lups = sum(s["fine_lups"] for s in stats)
-    value = lups * world / (ms / 1e3) / 1e9
+    value, sec = replica_aggregate(lups, ev0.elapsed_time(ev1) / 1e3, world, "cuda")
+    value /= 1e9
+    ms = sec * 1e3
     t_fine = sum(s["t_fine_ms"] for s in stats)
     launches = sum(s["launches"] for s in stats)
-    fine_launches = sum(s["iterations"] for s in stats) * p["f_steps"]
+    # the explicit F is one launch per fine step; the 1D implicit F one launch per batch
+    fine_launches = sum(s["iterations"] for s in stats) * (
+        1 if p.get("f_scheme") == "implicit" else p["f_steps"])
     # dominant kernel: the explicit fine step (its launches, timed by events on the
     # library's stream around every batched F)
     b_elem = 4 if is_mixed else 8
@@ -242,12 +464,17 @@ def run_ours(args, world, rank, local):
         ops = FP64_OPS_PER_LUP[dim] * lups
         roof = {"bound": "alu", "achieved": ops / (t_fine / 1e3) / 1e9, "peak": NOMINAL_FP64_OPS,
                 "unit": "Gop/s", "traffic": None,
-                "kernel": f"step{2 if dim == 2 else 3}d<double>",
+                "kernel": ("tri_solve (partition Thomas/PCR)" if dim == 1
+                           else f"step{2 if dim == 2 else 3}d<double>"),
                 "peak_kind": "nominal FP64 (1.25 TFLOP/s = 625 G DFMA/s)",
                 "hbm_view": {"achieved_gbs": alg_bytes / (t_fine / 1e3) / 1e9, "peak_gbs": hbm_peak,
                              "frac": alg_bytes / (t_fine / 1e3) / 1e9 / hbm_peak}}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["avg_launch_ms"] = t_fine / max(fine_launches, 1)
+    lups_per_launch = lups / max(fine_launches, 1)
+    roof["algorithmic_bytes_per_launch"] = 2 * b_elem * lups_per_launch
+    tpl = NCU_TRAFFIC_PER_LUP.get(args.workload)
+    roof["traffic"] = tpl * lups_per_launch if tpl else None
     out = {"metric": "fine GLUP/s", "value": value, "unit": "GLUP/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -272,6 +499,8 @@ def run_ours(args, world, rank, local):
     diff = (lam - sf).abs().max().item()
     out["max_abs_vs_serial_fine"] = diff
     del sf
+    if is_mixed:
+        out["mixed_vs_fp64"] = mixed_vs_fp64(pr, torch, p, u0, lam, ms / args.steps, args, local)
     # end-to-end through the host-buffer entry point (pinned host memory)
     if not args.no_e2e:
         u0h = torch.from_numpy(p["u0"].reshape(-1).copy()).pin_memory()
@@ -284,13 +513,8 @@ def run_ours(args, world, rank, local):
             _, st = pr.parareal_run_sync_host(ctx, u0h, outh)
             e_lups += st.fine_lups
         torch.cuda.synchronize()
-        te = time.perf_counter() - t0
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([te], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
-        out["e2e"] = {"value": e_lups * world / te / 1e9, "unit": "GLUP/s",
+        e_value, _ = replica_aggregate(e_lups, time.perf_counter() - t0, world, "cuda")
+        out["e2e"] = {"value": e_value / 1e9, "unit": "GLUP/s",
                       "h2d_bytes_per_step": M * 8, "d2h_bytes_per_step": (N + 1) * M * 8}
     out["clocks"] = clk.summary()
     pr.parareal_destroy(ctx)
@@ -314,6 +538,10 @@ def main():
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         return run_reference(args, world, rank)
+    if args.workload in ("heat2d_async", "heat3d_varkappa_async"):
+        return run_async_workload(args, local) if rank == 0 else 0
+    if args.workload == "heat2d_inverse":
+        return run_adjoint_workload(args, local) if rank == 0 else 0
     return run_ours(args, world, rank, local)
 
 

@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(ATHREADS) async_kernel(AsyncDev a) {
     const double* wn = w;
     int cg_it = 0;
     if (vG > vF) {
-      cg_it = cg_core(a.g, a.gst, a.var, a.gv, xs, w, a.rtol, a.maxit, ws, bar, a.C, tb, nullptr);
+      cg_it = cg_core(a.g, a.gst, a.var, a.gv, xs, w, a.rtol, a.maxit, ws, bar, a.C, tb);
       if (cg_it < 0) break;
       wn = ws.x;
     }

@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(CG_THREADS) cg_kernel(CgDev a) {
   const long long nt = (long long)gridDim.x * blockDim.x;
   if (a.mode == CG_CORRECT && t0 == 0) *a.delta = 0ull;
   const int it = cg_core(a.g, a.k, a.var != 0, a.gv, a.b, a.x0, a.rtol, a.maxit, a.ws,
-                         GridBarrier{}, gridDim.x, blockIdx.x, nullptr);
+                         GridBarrier{}, gridDim.x, blockIdx.x);
   // epilogue (x is final in the workspace)
   const double* x = a.ws.x;
   if (a.mode == CG_PLAIN) {

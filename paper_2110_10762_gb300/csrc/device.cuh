@@ -84,57 +84,46 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Block sum of three values into part[3*blk + {0,1,2}] (fixed order).
-__device__ __forceinline__ void block_sum3(double v0, double v1, double v2, double* part, int blk) {
-  __shared__ double sh[3][RED_THREADS / 32];
-  v0 = warp_sum(v0);
-  v1 = warp_sum(v1);
-  v2 = warp_sum(v2);
+// Block sum of NV (<= 3) values into part[3*blk + j] (fixed order).  Each value
+// costs 5 FP64 adds per thread in the warp tree, so callers reduce only what
+// they need (FP64 is the scarce pipe on this GPU).
+template <int NV>
+__device__ __forceinline__ void block_sum(const double (&v)[NV], double* part, int blk) {
+  __shared__ double sh[3][32];  // up to 32 warps per block
   const int wid = threadIdx.x / 32, lane = threadIdx.x % 32;
-  if (lane == 0) {
-    sh[0][wid] = v0;
-    sh[1][wid] = v1;
-    sh[2][wid] = v2;
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    const double s = warp_sum(v[j]);
+    if (lane == 0) sh[j][wid] = s;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-    for (int i = 0; i < (int)(blockDim.x / 32); ++i) {
-      s0 += sh[0][i];
-      s1 += sh[1][i];
-      s2 += sh[2][i];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      double s = 0.0;
+      for (int i = 0; i < (int)(blockDim.x / 32); ++i) s += sh[j][i];
+      part[3 * blk + j] = s;
     }
-    part[3 * blk] = s0;
-    part[3 * blk + 1] = s1;
-    part[3 * blk + 2] = s2;
   }
   __syncthreads();
 }
 
 // Sum of nblk block partials in a fixed order; identical result in every block.
-__device__ __forceinline__ void group_sum3(const double* part, int nblk, double& o0, double& o1,
-                                           double& o2) {
+template <int NV>
+__device__ __forceinline__ void group_sum(const double* part, int nblk, double (&o)[NV]) {
   __shared__ double res[3];
   if (threadIdx.x < 32) {
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-    for (int i = threadIdx.x; i < nblk; i += 32) {
-      s0 += __ldcg(part + 3 * i);
-      s1 += __ldcg(part + 3 * i + 1);
-      s2 += __ldcg(part + 3 * i + 2);
-    }
-    s0 = warp_sum(s0);
-    s1 = warp_sum(s1);
-    s2 = warp_sum(s2);
-    if (threadIdx.x == 0) {
-      res[0] = s0;
-      res[1] = s1;
-      res[2] = s2;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      double s = 0.0;
+      for (int i = threadIdx.x; i < nblk; i += 32) s += __ldcg(part + 3 * i + j);
+      s = warp_sum(s);
+      if (threadIdx.x == 0) res[j] = s;
     }
   }
   __syncthreads();
-  o0 = res[0];
-  o1 = res[1];
-  o2 = res[2];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) o[j] = res[j];
   __syncthreads();
 }
 
@@ -235,10 +224,9 @@ struct TeamBarrier {
 // Textbook CG for (I + dT A) x = b over a group of `nblk` blocks (this block
 // is number `blk`), stopping when ||r||_2 <= rtol ||b||_2, r == 0 or after
 // maxit iterations.  x0 may alias nothing it writes (x, r, p, q are the
-// group's workspace).  `abort_flag` (may be NULL) is sampled by block 0 at
-// every reduction and folded into the reduced values, so all blocks abandon
-// the solve at the same point.  Returns the iteration count, or -1 when
-// aborted / a barrier timed out.
+// group's workspace).  Every block computes bit-identical scalars (fixed-order
+// reductions), so all blocks take the same branches.  Returns the iteration
+// count, or -1 when a barrier timed out.
 struct CgWork {
   double* x;
   double* r;
@@ -250,16 +238,12 @@ struct CgWork {
 template <class Barrier>
 __device__ int cg_core(const Geom& g, const StencilConst& k, bool var, const StencilVar<double>& gv,
                        const double* __restrict__ b, const double* __restrict__ x0, double rtol,
-                       int maxit, const CgWork& ws, const Barrier& bar, int nblk, int blk,
-                       const int* abort_flag) {
+                       int maxit, const CgWork& ws, const Barrier& bar, int nblk, int blk) {
   const long long M = g.M;
   const long long t0 = blk * (long long)blockDim.x + threadIdx.x;
   const long long nt = (long long)nblk * blockDim.x;
   int parity = 0;
   auto part = [&]() { return ws.part + (size_t)parity * 3 * nblk; };
-  auto flag = [&]() -> double {
-    return (abort_flag && blk == 0 && threadIdx.x == 0 && ld_acquire(abort_flag)) ? 1.0 : 0.0;
-  };
   double s_rr = 0.0, s_bb = 0.0;
   for (long long i = t0; i < M; i += nt) {
     const double bi = b[i];
@@ -270,12 +254,16 @@ __device__ int cg_core(const Geom& g, const StencilConst& k, bool var, const Ste
     s_rr += ri * ri;
     s_bb += bi * bi;
   }
-  block_sum3(s_rr, s_bb, flag(), part(), blk);
+  {
+    const double v[2] = {s_rr, s_bb};
+    block_sum<2>(v, part(), blk);
+  }
   if (!bar.sync()) return -1;
-  double rr, bb, ab;
-  group_sum3(part(), nblk, rr, bb, ab);
+  double o2[2];
+  group_sum<2>(part(), nblk, o2);
   parity ^= 1;
-  if (ab != 0.0) return -1;
+  double rr = o2[0];
+  const double bb = o2[1];
   const double thresh = rtol * sqrt(bb);
   int it = 0;
   bool done = sqrt(rr) <= thresh || rr == 0.0 || maxit <= 0;
@@ -286,13 +274,15 @@ __device__ int cg_core(const Geom& g, const StencilConst& k, bool var, const Ste
       ws.q[i] = qi;
       s_pq += ws.p[i] * qi;
     }
-    block_sum3(s_pq, 0.0, flag(), part(), blk);
+    {
+      const double v[1] = {s_pq};
+      block_sum<1>(v, part(), blk);
+    }
     if (!bar.sync()) return -1;
-    double pq, u1;
-    group_sum3(part(), nblk, pq, u1, ab);
+    double o1[1];
+    group_sum<1>(part(), nblk, o1);
     parity ^= 1;
-    if (ab != 0.0) return -1;
-    const double alpha = rr / pq;
+    const double alpha = rr / o1[0];
     double s_rn = 0.0;
     for (long long i = t0; i < M; i += nt) {
       ws.x[i] += alpha * ws.p[i];
@@ -300,11 +290,14 @@ __device__ int cg_core(const Geom& g, const StencilConst& k, bool var, const Ste
       ws.r[i] = ri;
       s_rn += ri * ri;
     }
-    block_sum3(s_rn, 0.0, 0.0, part(), blk);
+    {
+      const double v[1] = {s_rn};
+      block_sum<1>(v, part(), blk);
+    }
     if (!bar.sync()) return -1;
-    double rr_new, u2;
-    group_sum3(part(), nblk, rr_new, u1, u2);
+    group_sum<1>(part(), nblk, o1);
     parity ^= 1;
+    const double rr_new = o1[0];
     ++it;
     done = sqrt(rr_new) <= thresh || rr_new == 0.0 || it >= maxit;
     if (!done) {

@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(NOALLOC_THREADS) noalloc_cg_kernel(NoallocArgs
   // cg_core writes every vector entry and every partial before reading it,
   // so nothing left in the array by an earlier call is ever read.
   const int it = cg_core(a.g, a.k, false, StencilVar<double>{}, a.b, a.x0, a.rtol, a.maxit, ws,
-                         GridBarrierNA{}, gridDim.x, blockIdx.x, nullptr);
+                         GridBarrierNA{}, gridDim.x, blockIdx.x);
   const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long nt = (long long)gridDim.x * blockDim.x;
   for (long long i = t0; i < M; i += nt) a.x[i] = ws.x[i];
