@@ -66,6 +66,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
     ap.add_argument("--profile", action="store_true",
                     help="run exactly one solve and nothing else (for ncu launch lists)")
+    ap.add_argument("--g-rtol", type=float, default=None,
+                    help="override the coarse CG tolerance of the workload")
+    ap.add_argument("--grid", default=None,
+                    help="override the grid, e.g. 160,160,160 (small cases for ncu captures)")
+    ap.add_argument("--slices", type=int, default=None, help="override N (small cases)")
     return ap.parse_args()
 
 
@@ -156,10 +161,17 @@ def dist_setup(args):
     return world, rank, local
 
 
+G_RTOL_OVERRIDE = None
+SIZE_OVERRIDE = {}
+
+
 def problem_of(name):
     from synthetic import preset
     base = {"heat2d_async": "heat2d_explicit"}.get(name, name)
-    return preset(base, "full")
+    p = preset(base, "full", **SIZE_OVERRIDE)
+    if G_RTOL_OVERRIDE is not None:
+        p["g_rtol"] = G_RTOL_OVERRIDE
+    return p
 
 
 def problem_struct(pr, p, u0, kappa=None, **over):
@@ -243,6 +255,8 @@ def mixed_vs_fp64(pr, torch, p, u0, lam_mixed, t_mixed_ms, args, local):
         err_64 = (lam64 - star).abs().max().item() / scale
         return {"t_mixed_ms": t_mixed_ms, "t_fp64_ms": t64, "speedup": t64 / t_mixed_ms,
                 "err_mixed": err_m, "err_fp64": err_64, "k_fp64": k64,
+                "fp64_t_fine_ms": st.t_fine_ms, "fp64_t_coarse_ms": st.t_coarse_ms,
+                "fp64_cg_iterations": st.cg_iterations, "g_rtol": p["g_rtol"],
                 "serial_fine_fp64_ms": sst.t_total_ms,
                 "accuracy_target": 1e-5, "mixed_meets_target": err_m <= 1e-5}
     finally:
@@ -534,7 +548,13 @@ def run_ours(args, world, rank, local):
 
 
 def main():
+    global G_RTOL_OVERRIDE
     args = parse()
+    G_RTOL_OVERRIDE = args.g_rtol
+    if args.grid:
+        SIZE_OVERRIDE["n"] = tuple(int(v) for v in args.grid.split(","))
+    if args.slices:
+        SIZE_OVERRIDE["N"] = args.slices
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         return run_reference(args, world, rank)

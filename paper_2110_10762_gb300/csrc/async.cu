@@ -69,7 +69,7 @@ struct AsyncDev {
   double* tv;                     // T * M      fine result v
   double* tcg;                    // T * 4 * M  CG x, r, p, q (FP64 fine ping-pong aliases r, p)
   double* tpart;                  // T * 6 * C
-  unsigned* bar;                  // T * 2
+  unsigned long long* bar;        // T      team barrier arrival counters
   int* ctrl;                      // T * 8  (two decision slots, seqlock words)
   unsigned long long* tdelta;     // T
   // global
@@ -156,9 +156,7 @@ __device__ void set_status(const AsyncDev& a, int st) {
 template <typename T>
 __device__ bool team_fine(const AsyncDev& a, const TeamBarrier& bar, const double* xs, double* v,
                           double* pp0, double* pp1, int tb) {
-  const long long M = a.g.M;
-  const long long t0 = tb * (long long)blockDim.x + threadIdx.x;
-  const long long nt = (long long)a.C * blockDim.x;
+  const Geom& g = a.g;
   const T c0 = T(a.fst.c0), rx = T(a.fst.rx), ry = T(a.fst.ry), rz = T(a.fst.rz);
   StencilVar<T> cv;
   if constexpr (sizeof(T) == 8) {
@@ -170,21 +168,27 @@ __device__ bool team_fine(const AsyncDev& a, const TeamBarrier& bar, const doubl
   T* buf1 = reinterpret_cast<T*>(pp1);
   const int S = a.f_steps;
   if (S == 1) {
-    for (long long i = t0; i < M; i += nt)
-      v[i] = double(fstep_at<T, double>(a.g, c0, rx, ry, rz, a.var, cv, xs, i));
+    for_each_point(g, tb, a.C, [&](int x, int y, int z, long long i) {
+      v[i] = double(fstep_xyz<T, double>(g, c0, rx, ry, rz, a.var, cv, xs, x, y, z, i));
+    });
     return bar.sync();
   }
-  for (long long i = t0; i < M; i += nt) buf0[i] = fstep_at<T, double>(a.g, c0, rx, ry, rz, a.var, cv, xs, i);
+  for_each_point(g, tb, a.C, [&](int x, int y, int z, long long i) {
+    buf0[i] = fstep_xyz<T, double>(g, c0, rx, ry, rz, a.var, cv, xs, x, y, z, i);
+  });
   if (!bar.sync()) return false;
   const T* src = buf0;
   for (int s = 1; s < S - 1; ++s) {
     T* dst = (src == buf0) ? buf1 : buf0;
-    for (long long i = t0; i < M; i += nt) dst[i] = fstep_at<T, T>(a.g, c0, rx, ry, rz, a.var, cv, src, i);
+    for_each_point(g, tb, a.C, [&](int x, int y, int z, long long i) {
+      dst[i] = fstep_xyz<T, T>(g, c0, rx, ry, rz, a.var, cv, src, x, y, z, i);
+    });
     if (!bar.sync()) return false;
     src = dst;
   }
-  for (long long i = t0; i < M; i += nt)
-    v[i] = double(fstep_at<T, T>(a.g, c0, rx, ry, rz, a.var, cv, src, i));
+  for_each_point(g, tb, a.C, [&](int x, int y, int z, long long i) {
+    v[i] = double(fstep_xyz<T, T>(g, c0, rx, ry, rz, a.var, cv, src, x, y, z, i));
+  });
   return bar.sync();
 }
 
@@ -198,8 +202,7 @@ __global__ void __launch_bounds__(ATHREADS) async_kernel(AsyncDev a) {
   const unsigned long long deadline = globaltimer() + a.timeout_ns;
   // barrier waits get a grace period beyond the run limit so that a normal
   // stop at the limit is not reported as a barrier failure
-  TeamBarrier bar{a.bar + 2 * team, a.bar + 2 * team + 1, a.C, deadline + 2000000000ull,
-                  a.barrier_err};
+  TeamBarrier bar{a.bar + team, a.C, deadline + 2000000000ull, a.barrier_err};
   int* ctrl = a.ctrl + 8 * team;
   double* tv = a.tv + (long long)team * M;
   double* cgx = a.tcg + (long long)team * 4 * M;
@@ -375,9 +378,9 @@ __global__ void async_init(AsyncDev a) {
       a.lastfg[t] = 0;
     }
   }
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < 2LL * a.T;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < a.T;
        t += (long long)gridDim.x * blockDim.x)
-    a.bar[t] = 0u;
+    a.bar[t] = 0ull;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < 8LL * a.T;
        t += (long long)gridDim.x * blockDim.x)
     a.ctrl[t] = 0;
@@ -432,7 +435,7 @@ int run_async(pr_ctx* c, const pr_async_opts* o, double* lam, pr_stats* st, pr_e
   const size_t d_ring = (size_t)N * RING * M, d_xs = (size_t)N * M, d_tv = (size_t)T * M,
                d_tcg = (size_t)T * 4 * M, d_tpart = (size_t)T * 6 * C, d_delta = N;
   const size_t n_dbl = d_ring + d_xs + d_tv + d_tcg + d_tpart + d_delta;
-  const size_t n_u64 = (size_t)N * RING + T + 1 + (log_cap ? 0 : 0);
+  const size_t n_u64 = (size_t)N * RING + T + 1 + T;  // ring_vis, tdelta, log_count, bar
   const size_t n_int = (size_t)N * RING + (N + 1) + 4 * (size_t)N + 2 * (size_t)T + 8 * (size_t)T + 3;
   const size_t bytes = n_dbl * 8 + n_u64 * 8 + n_int * 4 + 256;
   if (c->async_ws_bytes < bytes) {
@@ -484,6 +487,8 @@ int run_async(pr_ctx* c, const pr_async_opts* o, double* lam, pr_stats* st, pr_e
   up += T;
   a.log_count = up;
   up += 1;
+  a.bar = up;
+  up += T;
   int* ip = reinterpret_cast<int*>(up);
   a.ring_ver = ip;
   ip += (size_t)N * RING;
@@ -496,8 +501,7 @@ int run_async(pr_ctx* c, const pr_async_opts* o, double* lam, pr_stats* st, pr_e
   a.lastfg = ip;
   ip += N;
   ip += N;  // reserved
-  a.bar = reinterpret_cast<unsigned*>(ip);
-  ip += 2 * T;
+  ip += 2 * T;  // reserved
   a.ctrl = ip;
   ip += 8 * T;
   a.stop = ip++;

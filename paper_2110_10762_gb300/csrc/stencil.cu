@@ -114,10 +114,129 @@ __global__ void __launch_bounds__(BX* BY) step3d(const Tin* __restrict__ in, Tou
   }
 }
 
+// ---- FP32 3D step with 4 consecutive x points per thread (HBM-bound path of
+// the mixed form).  16-byte vector loads/stores (or 2 x 16 B for the FP64 input
+// of the first step and output of the last) keep 4x more bytes in flight per
+// instruction than the scalar kernel; the x-neighbours of a thread's 4 points
+// come from the adjacent lanes of its 16-lane row segment by warp shuffles.
+// Needs nx % 4 == 0 (and, for variable kappa, 16-byte aligned face arrays).
+constexpr int V4X = 16;  // threads along x (64 points)
+constexpr int V4Y = 8;   // rows
+constexpr int V4Z = 16;  // z planes per thread
+
+__device__ __forceinline__ float4 load4(const float* p) {
+  return __ldg(reinterpret_cast<const float4*>(p));
+}
+__device__ __forceinline__ float4 load4(const double* p) {
+  const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+  const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  return make_float4(static_cast<float>(a.x), static_cast<float>(a.y), static_cast<float>(b.x),
+                     static_cast<float>(b.y));
+}
+__device__ __forceinline__ void store4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ void store4(double* p, float4 v) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v.x, v.y);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v.z, v.w);
+}
+__device__ __forceinline__ float4 zero4() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+
+template <typename Tin, typename Tout, bool VAR>
+__global__ void __launch_bounds__(V4X* V4Y) step3d_v4(const Tin* __restrict__ in,
+                                                      Tout* __restrict__ out, int nx, int ny,
+                                                      int nz, int zchunks, long long M, float c0,
+                                                      float rx, float ry, float rz,
+                                                      StencilVar<float> cv) {
+  const int tx = threadIdx.x;
+  const int x4 = (blockIdx.x * V4X + tx) * 4;
+  const int y = blockIdx.y * V4Y + threadIdx.y;
+  const int slice = blockIdx.z / zchunks;
+  const int z0 = (blockIdx.z - slice * zchunks) * V4Z;
+  // no early return: every lane takes part in the shuffles
+  const bool valid = x4 < nx && y < ny;
+  const long long plane = (long long)nx * ny;
+  const Tin* u = in + (long long)slice * M;
+  Tout* o = out + (long long)slice * M;
+  const long long yx = (long long)y * nx + x4;
+  float4 b = zero4(), cur = zero4();
+  if (valid) {
+    if (z0 > 0) b = load4(u + (long long)(z0 - 1) * plane + yx);
+    cur = load4(u + (long long)z0 * plane + yx);
+  }
+  for (int j = 0; j < V4Z; ++j) {
+    const int z = z0 + j;
+    if (z >= nz) break;  // uniform over the block
+    const long long p = (long long)z * plane + yx;
+    float4 f = zero4(), s = zero4(), n = zero4();
+    if (valid) {
+      if (z + 1 < nz) f = load4(u + p + plane);
+      if (y > 0) s = load4(u + p - nx);
+      if (y + 1 < ny) n = load4(u + p + nx);
+    }
+    float w = __shfl_up_sync(0xffffffffu, cur.w, 1, V4X);
+    float e = __shfl_down_sync(0xffffffffu, cur.x, 1, V4X);
+    if (tx == 0) w = (valid && x4 > 0) ? static_cast<float>(__ldg(u + p - 1)) : 0.f;
+    if (tx == V4X - 1 || x4 + 4 >= nx) e = (valid && x4 + 4 < nx) ? static_cast<float>(__ldg(u + p + 4)) : 0.f;
+    float4 r;
+    if (!VAR) {
+      r.x = c0 * cur.x + rx * (w + cur.y) + ry * (s.x + n.x) + rz * (b.x + f.x);
+      r.y = c0 * cur.y + rx * (cur.x + cur.z) + ry * (s.y + n.y) + rz * (b.y + f.y);
+      r.z = c0 * cur.z + rx * (cur.y + cur.w) + ry * (s.z + n.z) + rz * (b.z + f.z);
+      r.w = c0 * cur.w + rx * (cur.z + e) + ry * (s.w + n.w) + rz * (b.w + f.w);
+    } else {
+      r = zero4();
+      if (valid) {
+        const float4 d = load4(cv.c0 + p);
+        const long long fx = ((long long)z * ny + y) * (nx + 1) + x4;
+        const float x0 = __ldg(cv.cx + fx), x1 = __ldg(cv.cx + fx + 1), x2 = __ldg(cv.cx + fx + 2),
+                    x3 = __ldg(cv.cx + fx + 3), x4f = __ldg(cv.cx + fx + 4);
+        const long long fy = ((long long)z * (ny + 1) + y) * nx + x4;
+        const float4 ys = load4(cv.cy + fy), yn = load4(cv.cy + fy + nx);
+        const float4 zb = load4(cv.cz + p), zf = load4(cv.cz + p + plane);
+        r.x = d.x * cur.x + x0 * w + x1 * cur.y + ys.x * s.x + yn.x * n.x + zb.x * b.x + zf.x * f.x;
+        r.y = d.y * cur.y + x1 * cur.x + x2 * cur.z + ys.y * s.y + yn.y * n.y + zb.y * b.y + zf.y * f.y;
+        r.z = d.z * cur.z + x2 * cur.y + x3 * cur.w + ys.z * s.z + yn.z * n.z + zb.z * b.z + zf.z * f.z;
+        r.w = d.w * cur.w + x3 * cur.z + x4f * e + ys.w * s.w + yn.w * n.w + zb.w * b.w + zf.w * f.w;
+      }
+    }
+    if (valid) store4(o + p, r);
+    b = cur;
+    cur = f;
+  }
+}
+
+bool v4_path_ok(const pr_ctx* c) {
+  const Geom& g = c->g;
+  if (g.dim != 3 || g.nx % 4 != 0) return false;
+  if (!c->var_kappa) return true;
+  // face arrays must start on 16-byte boundaries: (nx+1)*ny*nz and M multiples of 4
+  return ((long long)g.ny * g.nz) % 4 == 0;
+}
+
+template <typename Tin, typename Tout>
+cudaError_t launch_step_v4(const pr_ctx* c, const Tin* in, Tout* out, int count,
+                           const StencilVar<float>& cv) {
+  const Geom& g = c->g;
+  const int zchunks = (g.nz + V4Z - 1) / V4Z;
+  dim3 blk(V4X, V4Y);
+  dim3 grd((g.nx / 4 + V4X - 1) / V4X, (g.ny + V4Y - 1) / V4Y, count * zchunks);
+  const float c0 = static_cast<float>(c->fst.c0), rx = static_cast<float>(c->fst.rx),
+              ry = static_cast<float>(c->fst.ry), rz = static_cast<float>(c->fst.rz);
+  if (c->var_kappa)
+    step3d_v4<Tin, Tout, true><<<grd, blk, 0, c->stream>>>(in, out, g.nx, g.ny, g.nz, zchunks, g.M,
+                                                            c0, rx, ry, rz, cv);
+  else
+    step3d_v4<Tin, Tout, false><<<grd, blk, 0, c->stream>>>(in, out, g.nx, g.ny, g.nz, zchunks, g.M,
+                                                             c0, rx, ry, rz, cv);
+  return cudaGetLastError();
+}
+
 template <typename Tin, typename Tout, typename T>
 cudaError_t launch_step(const pr_ctx* c, const Tin* in, Tout* out, int count,
                         const StencilVar<T>& cv) {
   const Geom& g = c->g;
+  if constexpr (sizeof(T) == 4) {
+    if (v4_path_ok(c)) return launch_step_v4<Tin, Tout>(c, in, out, count, cv);
+  }
   const T c0 = static_cast<T>(c->fst.c0), rx = static_cast<T>(c->fst.rx),
           ry = static_cast<T>(c->fst.ry), rz = static_cast<T>(c->fst.rz);
   dim3 blk(BX, BY);

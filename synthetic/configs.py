@@ -51,8 +51,11 @@ def _u0(name: str, n) -> np.ndarray:
     return gen.smoothed_noise_3d((n[2], n[1], n[0]), seed=seed)
 
 
-def preset(name: str, scale: str = "full") -> dict:
-    """Return the problem dict (sizes, steps, dt, T, u0, kappa) for a workload."""
+def preset(name: str, scale: str = "full", **override) -> dict:
+    """Return the problem dict (sizes, steps, dt, T, u0, kappa) for a workload.
+
+    `override` replaces recipe entries (e.g. n, N, f_steps) before the inputs
+    are generated, for profiling the same recipe at another size."""
     base = dict(PRESETS[name])
     small = base.pop("small")
     tiny = base.pop("tiny")
@@ -62,6 +65,7 @@ def preset(name: str, scale: str = "full") -> dict:
         base.update(tiny)
     elif scale != "full":
         raise ValueError(scale)
+    base.update(override)
     dim = base["dim"]
     n = tuple(base["n"])
     h = [1.0 / (m + 1) for m in n]

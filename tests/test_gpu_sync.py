@@ -79,6 +79,30 @@ def test_fine_propagator_mixed_precision(case):
         assert err > 1e-12  # the steps really ran in FP32
 
 
+@pytest.mark.parametrize("n,var", [((68, 12, 9), False), ((68, 12, 9), True),
+                                   ((64, 17, 33), False), ((4, 3, 4), True)])
+def test_fine_fp32_vectorized_3d(n, var):
+    """FP32 3D steps with 4 x-points per thread (nx % 4 == 0): ragged x/y/z tiles."""
+    rng = np.random.default_rng(15)
+    h = tuple(1.0 / (m + 1) for m in n)
+    shape = tuple(reversed(n))
+    kap = np.exp(0.3 * rng.standard_normal(tuple(s + 2 for s in shape))) if var else None
+    kmax = 1.0 if kap is None else float(kap.max())
+    p = dict(dim=3, n=n, h=h, N=3, f_steps=5, dt=0.8 * min(h) ** 2 / (6 * kmax),
+             f_scheme="explicit", g_solver="cg", g_rtol=1e-10, f_prec=32, kappa=kap,
+             u0=rng.standard_normal(shape), tol=0.0)
+    P = oracle_props(p)
+    X = rng.standard_normal((3,) + shape)
+    with Ctx(p) as c:
+        xin = dev(X)
+        out = torch().empty_like(xin)
+        pr.parareal_fine(c.ctx, xin, out, 3)
+        got = host(out).reshape(X.shape)
+    for s in range(3):
+        err = rel_l2(got[s], P.F(X[s]))
+        assert 1e-12 < err < MIXED_TOL, (s, err)
+
+
 @pytest.mark.parametrize("case", list(CASES))
 def test_coarse_propagator(case):
     p = CASES[case]()
