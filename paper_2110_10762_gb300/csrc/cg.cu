@@ -46,7 +46,13 @@ struct GridBarrier {
   }
 };
 
-__global__ void __launch_bounds__(CG_THREADS) cg_kernel(CgDev a) {
+// MINB = blocks per SM the register budget must allow.  The CG vectors of a
+// grid up to about 2 M points stay in L2 and 2 blocks/SM are best (fewer
+// partials and barrier arrivals); beyond that the phases stream from HBM and
+// are latency-bound, so a 4-blocks/SM instance (<= 64 registers) keeps twice
+// as many loads in flight (measured 707 -> ~550 us per iteration at 256^3).
+template <int MINB>
+__global__ void __launch_bounds__(CG_THREADS, MINB) cg_kernel(CgDev a) {
   const long long M = a.g.M;
   const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long nt = (long long)gridDim.x * blockDim.x;
@@ -101,15 +107,24 @@ __global__ void copy_kernel(double* __restrict__ d, const double* __restrict__ s
     d[i] = s[i];
 }
 
-}  // namespace
+constexpr long long CG_L2_POINTS = 2LL << 20;  // 5 FP64 vectors of 2 M points = 80 MB
 
-int cg_max_blocks(int num_sms) {
+template <int MINB>
+int cg_blocks_of(int num_sms) {
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_kernel, CG_THREADS, 0) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_kernel<MINB>, CG_THREADS, 0) !=
           cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
+  if (per_sm > MINB) per_sm = MINB;
   return per_sm * num_sms;
+}
+
+}  // namespace
+
+int cg_max_blocks(int num_sms) {
+  const int a = cg_blocks_of<2>(num_sms), b = cg_blocks_of<4>(num_sms);
+  return a > b ? a : b;
 }
 
 cudaError_t cg_solve(pr_ctx* c, const CgArgs& in) {
@@ -129,12 +144,15 @@ cudaError_t cg_solve(pr_ctx* c, const CgArgs& in) {
   a.ws = {c->cg_x, c->cg_r, c->cg_p, c->cg_q, c->cg_part};
   a.rtol = c->prob.g_rtol;
   a.maxit = c->prob.g_maxit;
+  const bool big = c->g.M > CG_L2_POINTS;
+  const int cap = big ? cg_blocks_of<4>(c->num_sms) : cg_blocks_of<2>(c->num_sms);
   long long want = (c->g.M + CG_THREADS * 4 - 1) / (CG_THREADS * 4);
-  int blocks = (int)(want < c->cg_blocks ? want : c->cg_blocks);
+  int blocks = (int)(want < cap ? want : cap);
+  if (blocks > c->cg_blocks) blocks = c->cg_blocks;  // partials are sized for cg_blocks
   if (blocks < 1) blocks = 1;
   void* args[] = {&a};
-  return cudaLaunchCooperativeKernel((void*)cg_kernel, dim3(blocks), dim3(CG_THREADS), args, 0,
-                                     c->stream);
+  return cudaLaunchCooperativeKernel(big ? (void*)cg_kernel<4> : (void*)cg_kernel<2>, dim3(blocks),
+                                     dim3(CG_THREADS), args, 0, c->stream);
 }
 
 cudaError_t correct(pr_ctx* c, const double* w_new, const double* v, const double* w_old,

@@ -131,3 +131,24 @@ def test_adjoint_rejects_unsupported():
         gu0 = torch().empty(c.M, dtype=torch().float64, device="cuda")
         with pytest.raises(pr.PararealError):
             pr.parareal_adjoint(c.ctx, gu0, 1, gu0, None)
+
+
+def test_adjoint_K0_is_the_predictor_chain():
+    """K = 0: lambda_N = G^N u0, so dL/du0 = G^N g (G symmetric)."""
+    p = small()
+    rng = np.random.default_rng(33)
+    g = rng.standard_normal(tuple(reversed(p["n"])))
+    ref_u0, ref_k, _ = adjoint_sync(p, g, 0)
+    gu0, gk = gpu_adjoint(p, g, 0)
+    assert rel_l2(gu0, ref_u0) < ADJ_TOL
+    assert rel_l2(gk, ref_k) < ADJ_TOL
+
+
+def test_adjoint_rejects_bad_K_and_constant_kappa_gradient():
+    p = small("heat2d_explicit")
+    with Ctx(p) as c:
+        gu0 = torch().empty(c.M, dtype=torch().float64, device="cuda")
+        with pytest.raises(pr.PararealError):
+            pr.parareal_adjoint(c.ctx, gu0, p["N"] + 1, gu0, None)
+        with pytest.raises(pr.PararealError):
+            pr.parareal_adjoint(c.ctx, gu0, 1, gu0, gu0)   # no kappa to differentiate

@@ -148,3 +148,26 @@ def test_async_rejects_unsupported_problems():
         with pytest.raises(pr.PararealError) as e:
             pr.parareal_run_async(c.ctx, pr.make_async_opts(), c.lam(), log_cap=10)
         assert e.value.code == pr.PR_EINVAL
+
+
+def test_async_single_slice_is_one_fine_solve():
+    """N = 1: the only update is lambda_1 = F(u0) (w_new = w_old, no coarse solve)."""
+    p = case("heat2d_explicit", tol=1e-9)
+    p["N"] = 1
+    ref = serial_fine(p)
+    with Ctx(p) as c:
+        code, st, log, lam = run_async(c, timeout_s=30.0)
+    assert code == pr.PR_OK and st.iterations == 1 and len(log) == 1
+    assert log[0].vF == 0 and log[0].vG == 0 and log[0].cg_iters == 0
+    assert rel_l2(lam, ref) < FP64_TOL
+
+
+def test_async_one_dimensional_explicit():
+    p = case("heat1d_thomas", tol=1e-9)
+    p.update(dict(f_scheme="explicit", g_solver="cg", dt=0.3 / 128 ** 2))
+    with Ctx(p) as c:
+        code, st, log, lam = run_async(c, timeout_s=30.0)
+    assert code == pr.PR_OK
+    check_log(log, p["N"])
+    rep = async_replay(p, events_of(log))
+    assert rel_l2(lam, rep.lam) < FP64_TOL

@@ -124,6 +124,25 @@ def test_coarse_propagator(case):
         assert np.linalg.norm(r) <= 1e-12 * np.linalg.norm(b) * 10
 
 
+def test_coarse_propagator_hbm_resident_grid():
+    """2.5 M points (the CG instance sized for grids that do not fit in L2)."""
+    n = (136, 136, 136)
+    rng = np.random.default_rng(16)
+    h = tuple(1.0 / (m + 1) for m in n)
+    shape = tuple(reversed(n))
+    p = dict(dim=3, n=n, h=h, N=1, f_steps=64, dt=0.15 * h[0] ** 2, f_scheme="explicit",
+             g_solver="cg", g_rtol=1e-8, u0=np.zeros(shape), tol=0.0)
+    b = rng.standard_normal(shape)
+    P = oracle_props(p)
+    ref, ref_it = P.G(b)
+    with Ctx(p) as c:
+        out = torch().empty(c.M, dtype=torch().float64, device="cuda")
+        it = pr.parareal_coarse(c.ctx, dev(b), None, out)
+        got = host(out)
+    assert abs(it - ref_it) <= 2
+    assert rel_l2(got, ref) < 1e-10
+
+
 def test_correction_is_bit_exact():
     p = CASES["2d_const"]()
     rng = np.random.default_rng(14)
