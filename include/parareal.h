@@ -183,6 +183,19 @@ int parareal_correct(pr_ctx* ctx, const double* w_new_dev, const double* v_dev,
 int parareal_adjoint(pr_ctx* ctx, const double* dL_dlamN_dev, int K, double* grad_u0_dev,
                      double* grad_kappa_dev);
 
+/* Scheduling options (they never change results, only when work runs):
+ *  PR_OPT_PIPELINE (0/1, default 0): parareal_run_sync overlaps the fine
+ *    propagation of iteration k+1 with the coarse sweep of iteration k (slice
+ *    i's fine input lam_{i-1}^{k+1} is final as soon as the sweep has passed
+ *    slice i-1, as in the processor schedule of Algorithm 1, §4.1).  The fine
+ *    work runs on a low-priority stream in slice chunks; results are bitwise
+ *    identical to the plain schedule.  Needs N*M more doubles.
+ *  PR_OPT_PIPELINE_CHUNKS (1..1024, default 8): slice chunks per fine batch.
+ *  PR_OPT_CG_BLOCKS_PER_SM (0 = automatic): cap on the co-resident blocks per
+ *    SM of the coarse CG kernel (leaves room for concurrent fine work). */
+enum pr_option { PR_OPT_PIPELINE = 1, PR_OPT_PIPELINE_CHUNKS = 2, PR_OPT_CG_BLOCKS_PER_SM = 3 };
+int parareal_set_option(pr_ctx* ctx, int option, double value);
+
 /* Per-slice statistics of the last run (host arrays of N entries, may be NULL):
  * k_i (async update counts; sync: k for every slice) and delta_i. */
 int parareal_slice_stats(pr_ctx* ctx, int* k_host, double* delta_host);

@@ -16,6 +16,7 @@ STATUS_NAMES = {0: "PR_OK", 1: "PR_EINVAL", 2: "PR_ENOMEM", 3: "PR_ECUDA", 4: "P
                 5: "PR_ENOTCONV", 6: "PR_ESTATE", 7: "PR_ELOGFULL"}
 PR_EXPLICIT_EULER, PR_IMPLICIT_EULER = 0, 1
 PR_SOLVER_THOMAS, PR_SOLVER_CG = 0, 1
+PR_OPT_PIPELINE, PR_OPT_PIPELINE_CHUNKS, PR_OPT_CG_BLOCKS_PER_SM = 1, 2, 3
 
 
 class pr_problem(C.Structure):
@@ -67,6 +68,7 @@ EXPORTS = {
                                    C.POINTER(C.c_double)]),
     "parareal_adjoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "parareal_slice_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    "parareal_set_option": (C.c_int, [C.c_void_p, C.c_int, C.c_double]),
     "parareal_coarse_noalloc": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.c_double, C.c_void_p,
                                           C.c_void_p, C.c_void_p, C.c_double, C.c_int,
                                           C.POINTER(C.c_int), C.c_void_p]),

@@ -177,6 +177,10 @@ def parareal_adjoint(ctx, dL_dlamN, K: int, grad_u0, grad_kappa=None):
                                                _ptr(grad_kappa)))
 
 
+def parareal_set_option(ctx, option: int, value: float):
+    return _check(ctx, _lib().parareal_set_option(ctx, int(option), float(value)))
+
+
 def parareal_slice_stats(ctx, N: int):
     k = (C.c_int * N)()
     d = (C.c_double * N)()

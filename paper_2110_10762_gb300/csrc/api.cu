@@ -48,6 +48,7 @@ void free_problem(pr_ctx* c) {
   c->adj_ws_bytes = 0;
   tri_free(&c->tri_f);
   tri_free(&c->tri_g);
+  pipeline_free(c);
   c->fvar = {};
   c->gvar = {};
   c->fvar32 = {};
@@ -351,11 +352,31 @@ int parareal_serial_fine(pr_ctx* c, double* lam, pr_stats* st) {
   return PR_OK;
 }
 
+int parareal_set_option(pr_ctx* c, int option, double value) {
+  if (!c) return PR_EINVAL;
+  switch (option) {
+    case PR_OPT_PIPELINE:
+      c->opt_pipeline = value != 0.0 ? 1 : 0;
+      return PR_OK;
+    case PR_OPT_PIPELINE_CHUNKS:
+      if (!(value >= 1.0 && value <= 1024.0)) return fail(c, PR_EINVAL, "chunks must be in [1, 1024]");
+      c->opt_chunks = (int)value;
+      return PR_OK;
+    case PR_OPT_CG_BLOCKS_PER_SM:
+      if (!(value >= 0.0 && value <= 32.0)) return fail(c, PR_EINVAL, "blocks per SM must be in [0, 32]");
+      c->opt_cg_bps = (int)value;
+      return PR_OK;
+    default:
+      return fail(c, PR_EINVAL, "unknown option");
+  }
+}
+
 int parareal_run_sync(pr_ctx* c, double* lam, pr_stats* st) {
   int s = check_ready(c);
   if (s) return s;
   if (!lam || !aligned16(lam)) return fail(c, PR_EINVAL, "bad pointer");
   cudaSetDevice(c->device);
+  if (c->opt_pipeline) return run_sync_pipelined(c, lam, st);
   const pr_problem& p = c->prob;
   const long long M = c->g.M;
   const int N = p.N;

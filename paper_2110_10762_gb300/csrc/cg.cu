@@ -145,7 +145,9 @@ cudaError_t cg_solve(pr_ctx* c, const CgArgs& in) {
   a.rtol = c->prob.g_rtol;
   a.maxit = c->prob.g_maxit;
   const bool big = c->g.M > CG_L2_POINTS;
-  const int cap = big ? cg_blocks_of<4>(c->num_sms) : cg_blocks_of<2>(c->num_sms);
+  int cap = big ? cg_blocks_of<4>(c->num_sms) : cg_blocks_of<2>(c->num_sms);
+  // a caller-chosen blocks-per-SM cap leaves room for concurrent kernels
+  if (c->opt_cg_bps > 0 && c->opt_cg_bps * c->num_sms < cap) cap = c->opt_cg_bps * c->num_sms;
   long long want = (c->g.M + CG_THREADS * 4 - 1) / (CG_THREADS * 4);
   int blocks = (int)(want < cap ? want : cap);
   if (blocks > c->cg_blocks) blocks = c->cg_blocks;  // partials are sized for cg_blocks

@@ -92,6 +92,14 @@ struct pr_ctx {
   std::vector<double> last_delta;
   cudaEvent_t ev[6] = {};
   std::string err;
+  // options (parareal_set_option)
+  int opt_pipeline = 0;      // overlap F of iteration k+1 with the coarse sweep of k
+  int opt_chunks = 8;        // slice chunks per pipelined fine batch
+  int opt_cg_bps = 0;        // CG blocks per SM (0 = automatic)
+  // pipelined driver resources (created lazily)
+  cudaStream_t s_sweep = nullptr, s_fine = nullptr;
+  double* v2 = nullptr;      // second fine-output buffer (N*M)
+  std::vector<cudaEvent_t> pev;
   // async / adjoint workspaces are allocated lazily by their drivers
   void* async_ws = nullptr;
   size_t async_ws_bytes = 0;
@@ -147,6 +155,10 @@ cudaError_t correct(pr_ctx* c, const double* w_new, const double* v, const doubl
                     double* lam, unsigned long long* delta);
 // Generic dense helpers
 cudaError_t vec_copy(pr_ctx* c, double* dst, const double* src, long long n);
+
+// ---- pipelined synchronous driver (pipeline.cu)
+int run_sync_pipelined(pr_ctx* c, double* lam, pr_stats* st);
+void pipeline_free(pr_ctx* c);
 
 // ---- asynchronous persistent kernel (async.cu)
 int run_async(pr_ctx* c, const pr_async_opts* o, double* lam_out, pr_stats* st, pr_event* log,

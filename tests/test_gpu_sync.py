@@ -308,6 +308,49 @@ def test_invalid_problems_are_rejected():
         pr.parareal_destroy(ctx)
 
 
+@pytest.mark.parametrize("case,chunks,bps", [("2d_const", 8, 0), ("2d_var", 3, 1),
+                                             ("3d_var", 1, 0), ("1d_thomas", 4, 0),
+                                             ("3d_const", 100, 2)])
+def test_pipelined_schedule_is_bitwise_identical(case, chunks, bps):
+    """Overlapping F of iteration k+1 with the sweep of k changes timing only."""
+    p = CASES[case]()
+    p["tol"] = 1e-9
+    if case == "3d_var":
+        p["f_prec"] = 32
+    with Ctx(p) as c:
+        lam_a = c.lam()
+        code_a, st_a = pr.parareal_run_sync(c.ctx, lam_a)
+        pr.parareal_set_option(c.ctx, pr.PR_OPT_PIPELINE, 1)
+        pr.parareal_set_option(c.ctx, pr.PR_OPT_PIPELINE_CHUNKS, chunks)
+        pr.parareal_set_option(c.ctx, pr.PR_OPT_CG_BLOCKS_PER_SM, bps)
+        for _ in range(2):
+            lam_b = c.lam()
+            code_b, st_b = pr.parareal_run_sync(c.ctx, lam_b)
+            assert st_b.iterations == st_a.iterations
+            assert st_b.fine_lups == st_a.fine_lups
+            if bps == 0:
+                assert torch().equal(lam_a, lam_b)
+            else:   # fewer CG blocks: same arithmetic, another summation order
+                assert rel_l2(host(lam_b), host(lam_a)) < FP64_TOL
+
+
+def test_pipelined_schedule_with_iteration_cap_and_bad_options():
+    p = CASES["2d_const"]()
+    p["tol"] = 1e-14
+    p["max_iter"] = 3
+    with Ctx(p) as c:
+        lam_a = c.lam()
+        code_a, st_a = pr.parareal_run_sync(c.ctx, lam_a)
+        pr.parareal_set_option(c.ctx, pr.PR_OPT_PIPELINE, 1)
+        lam_b = c.lam()
+        code_b, st_b = pr.parareal_run_sync(c.ctx, lam_b)
+        assert code_a == code_b == pr.PR_ENOTCONV and st_b.iterations == 3
+        assert torch().equal(lam_a, lam_b)
+        for opt, val in [(99, 1), (pr.PR_OPT_PIPELINE_CHUNKS, 0), (pr.PR_OPT_CG_BLOCKS_PER_SM, -1)]:
+            with pytest.raises(pr.PararealError):
+                pr.parareal_set_option(c.ctx, opt, val)
+
+
 def test_notconv_status_when_max_iter_stops_early():
     p = CASES["2d_const"]()
     p["tol"] = 1e-14
