@@ -279,14 +279,17 @@ __device__ int cg_core(const Geom& g, const StencilConst& k, bool var, const Ste
   int it = 0;
   bool done = sqrt(rr) <= thresh || rr == 0.0 || maxit <= 0;
   while (!done) {
-    double s_pq = 0.0;
+    // two accumulators per thread break the dependent FMA chain of the dot product
+    double s_a = 0.0, s_b = 0.0;
     for_each_point(g, blk, nblk, [&](int x, int y, int z, long long i) {
       const double qi = gop_xyz(g, k, var, gv, ws.p, x, y, z, i);
       ws.q[i] = qi;
-      s_pq += ws.p[i] * qi;
+      const double t = s_a + ws.p[i] * qi;  // alternate the two accumulators
+      s_a = s_b;
+      s_b = t;
     });
     {
-      const double v[1] = {s_pq};
+      const double v[1] = {s_a + s_b};
       block_sum<1>(v, part(), blk);
     }
     if (!bar.sync()) return -1;
@@ -294,15 +297,27 @@ __device__ int cg_core(const Geom& g, const StencilConst& k, bool var, const Ste
     group_sum<1>(part(), nblk, o1);
     parity ^= 1;
     const double alpha = rr / o1[0];
-    double s_rn = 0.0;
-    for (long long i = t0; i < M; i += nt) {
+    double s_rn[2] = {0.0, 0.0};
+    long long i = t0;
+    for (; i + nt < M; i += 2 * nt) {
+      const long long j = i + nt;
+      ws.x[i] += alpha * ws.p[i];
+      ws.x[j] += alpha * ws.p[j];
+      const double ri = ws.r[i] - alpha * ws.q[i];
+      const double rj = ws.r[j] - alpha * ws.q[j];
+      ws.r[i] = ri;
+      ws.r[j] = rj;
+      s_rn[0] += ri * ri;
+      s_rn[1] += rj * rj;
+    }
+    if (i < M) {
       ws.x[i] += alpha * ws.p[i];
       const double ri = ws.r[i] - alpha * ws.q[i];
       ws.r[i] = ri;
-      s_rn += ri * ri;
+      s_rn[0] += ri * ri;
     }
     {
-      const double v[1] = {s_rn};
+      const double v[1] = {s_rn[0] + s_rn[1]};
       block_sum<1>(v, part(), blk);
     }
     if (!bar.sync()) return -1;

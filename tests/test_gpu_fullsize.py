@@ -1,0 +1,80 @@
+"""Parity at the full workload sizes, in the launch configuration bench.py times.
+
+The oracle cannot run a whole Parareal solve at these sizes, so the checks
+use outputs it can compute one at a time (one fine propagation, one coarse
+residual) and properties that hold at any size:
+  * after k >= 1 iterations slice 1 is exact: lambda_1 = F(u0) (§3.2);
+  * at convergence lambda_i - F(lambda_{i-1}) is of the order of the last
+    increments (Eq. (11) with lambda^k ~ lambda^{k-1});
+  * the coarse solve meets its residual bound, measured with the oracle's
+    operator.
+"""
+import numpy as np
+import pytest
+
+from oracle import heat
+from synthetic import preset
+
+from .gpu_util import Ctx, dev, host, rel_l2, torch
+
+pr = pytest.importorskip("paper_2110_10762_gb300")
+
+pytestmark = pytest.mark.gpu
+
+
+def test_heat2d_bench_workload_sampled_parity():
+    """1024^2, N = 64, F = 256 explicit steps, CG rtol 1e-10, tol 1e-10 (the bench line)."""
+    p = preset("heat2d_explicit", "full")
+    P = heat.Propagators(p)
+    shape = tuple(reversed(p["n"]))
+    with Ctx(p) as c:
+        lam = c.lam()
+        code, st = pr.parareal_run_sync(c.ctx, lam)
+        L = host(lam).reshape((p["N"] + 1,) + shape)
+        # coarse solve on the last state: residual of the GPU solution by the oracle's operator
+        out = torch().empty(c.M, dtype=torch().float64, device="cuda")
+        pr.parareal_coarse(c.ctx, dev(L[-2]), None, out)
+        x = host(out).reshape(shape)
+    assert code == pr.PR_OK and st.converged and 1 <= st.iterations < p["N"]
+    assert np.array_equal(L[0], p["u0"])
+    assert rel_l2(L[1], P.F(p["u0"])) < 1e-12
+    for i in (2, p["N"] // 2, p["N"]):
+        gap = np.max(np.abs(L[i] - P.F(L[i - 1])))
+        assert gap < 20 * p["tol"], (i, gap)
+    r = L[-2] - (x + P.dT * heat.apply_A(x, P.h, None))
+    assert np.linalg.norm(r) <= 1.01 * p["g_rtol"] * np.linalg.norm(L[-2])
+
+
+def test_heat3d_mixed_workload_sampled_parity():
+    """256^3, N = 128, FP32 fine / FP64 coarse, tol 1e-5: slice 1 and the accuracy target."""
+    p = preset("heat3d_mixed", "full")
+    p["g_rtol"] = 1e-7
+    P64 = heat.Propagators(p)
+    shape = tuple(reversed(p["n"]))
+    with Ctx(p) as c:
+        lam = c.lam()
+        code, st = pr.parareal_run_sync(c.ctx, lam)
+        l1 = host(lam[c.M:2 * c.M]).reshape(shape)
+        lN = host(lam[p["N"] * c.M:]).reshape(shape)
+        lNm1 = host(lam[(p["N"] - 1) * c.M:p["N"] * c.M]).reshape(shape)
+    assert code == pr.PR_OK and st.converged
+    ref1 = P64.F(p["u0"])                      # FP64 oracle
+    assert rel_l2(l1, ref1) < 1e-5
+    scale = np.max(np.abs(ref1))
+    gap = np.max(np.abs(lN - P64.F(lNm1))) / scale
+    assert gap < 1e-5, gap
+
+
+def test_heat3d_varkappa_fp32_fine_step_full_size():
+    """192^3 variable kappa, FP32 vector kernel (one slice, 32 steps) vs the FP64 oracle."""
+    p = preset("heat3d_varkappa_async", "full")
+    P = heat.Propagators(dict(p, f_prec=64))
+    rng = np.random.default_rng(17)
+    x0 = p["u0"] + 0.01 * rng.standard_normal(p["u0"].shape)
+    with Ctx(p) as c:
+        xin = dev(x0)
+        out = torch().empty_like(xin)
+        pr.parareal_fine(c.ctx, xin, out, 1)
+        got = host(out).reshape(x0.shape)
+    err = rel_l2(got, P.F(x0))
+    assert 1e-12 < err < 1e-5, err
