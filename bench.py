@@ -19,6 +19,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -44,15 +45,30 @@ WORKLOADS = {
     "heat2d_inverse": "2D inverse heat 512x512, variable kappa, N=32, F=128, K=6 Parareal "
                       "iterations: loss + discrete-adjoint gradient wrt u0 and kappa, FP64",
 }
-# FP64-pipe operations per fine cell update (DADD/DMUL/DFMA each one issue slot):
-# 2D 5-point = 2 DADD + 1 DMUL + 2 DFMA; 3D 7-point = 3 + 1 + 3; 1D implicit step by the
-# partition solver = 2 (forward) + 1 (back) + 2 (rebuild) per unknown.
-FP64_OPS_PER_LUP = {1: 5, 2: 5, 3: 7}
+# FP64-pipe operations per fine cell update (DADD/DMUL/DFMA each one issue slot).
+# Constant kappa, explicit: the library runs the scaled form (states carried as
+# u / rx^j, which removes the x multiplier): 1D 1 DADD + 1 DFMA, 2D 2 DADD + 2 DFMA,
+# 3D 3 DADD + 3 DFMA, plus one DMUL on the steps that return to u (every R steps and
+# the last one, R = floor(100 / log10(1/rx))).  The asynchronous kernel's fine steps
+# use the plain form (scaled=False): 1 DMUL + d DADD + d DFMA.  Variable kappa:
+# 1 DMUL + 2d DFMA.  1D implicit step by the partition solver: 2 (forward) + 1 (back)
+# + 2 (rebuild).
+def fp64_ops_per_lup(p, scaled=True):
+    dim = p["dim"]
+    if p.get("f_scheme") == "implicit":
+        return 5.0
+    if p.get("kappa") is not None or not scaled:
+        return 1.0 + 2 * dim
+    rx = p["dt"] / (1.0 / (p["n"][0] + 1)) ** 2
+    R = max(1, int(math.floor(100.0 / math.log10(1.0 / rx))))
+    return 2.0 * dim + math.ceil(p["f_steps"] / R) / p["f_steps"]
+
+
 NOMINAL_FP64_OPS = 625.0  # G FP64-pipe ops/s: 1.25 TFLOP/s nominal / 2 flops per DFMA
 # DRAM bytes (read + write) per cell update of the dominant kernel, from one ncu capture
-# of the unchanged kernel (profiles/step2d_fp64_heat2d_1024x1024.md: 1017.0 MB for
-# 63 x 1048576 updates); None where no capture of the current kernel exists.
-NCU_TRAFFIC_PER_LUP = {"heat2d_explicit": 1017.0e6 / (63 * 1048576)}
+# of the current kernel; None where no capture of the current kernel exists.
+# (profiles/step2d_fp64_heat2d_1024x1024.md: 1016.3 MB for 63 x 1048576 updates).
+NCU_TRAFFIC_PER_LUP = {"heat2d_explicit": 1016.3e6 / (63 * 1048576)}
 
 
 def parse():
@@ -74,6 +90,8 @@ def parse():
     ap.add_argument("--pipeline", action="store_true",
                     help="overlap F of iteration k+1 with the coarse sweep of iteration k")
     ap.add_argument("--chunks", type=int, default=8, help="slice chunks per pipelined F batch")
+    ap.add_argument("--lazy", action="store_true",
+                    help="async workloads: skip re-updates that a newer input will supersede")
     ap.add_argument("--cg-bps", type=int, default=0,
                     help="CG blocks per SM under the pipeline (0 = automatic)")
     return ap.parse_args()
@@ -306,7 +324,8 @@ def run_async_workload(args, local):
         t_ms, _ = _timed(torch, lambda: pr.parareal_fine(ctx, x, y, 1), 3)
         unit_ns = t_ms * 1e6 / p["f_steps"]
         delays = torch.from_numpy(delay_table(N, 64, seed=p["delay_seed"])).cuda()
-    opts = pr.make_async_opts(timeout_s=300.0, delays=delays, delay_unit_ns=unit_ns)
+    opts = pr.make_async_opts(timeout_s=300.0, delays=delays, delay_unit_ns=unit_ns,
+                              lazy=args.lazy)
     if args.profile:
         code, st, log = pr.parareal_run_async(ctx, opts, lam, log_cap=1 << 20)
         torch.cuda.synchronize()
@@ -342,7 +361,7 @@ def run_async_workload(args, local):
     value = lups / (t_async * args.steps / 1e3) / 1e9
     cg_ops = {2: 10.3, 3: 12.3}[p["dim"]]
     fp64_ops = st.cg_iterations * M * cg_ops + (
-        st.fine_lups * FP64_OPS_PER_LUP[p["dim"]] if p.get("f_prec", 64) == 64 else 0)
+        st.fine_lups * fp64_ops_per_lup(p, scaled=False) if p.get("f_prec", 64) == 64 else 0)
     roof = {"bound": "alu", "kernel": "async_kernel", "unit": "Gop/s",
             "achieved": fp64_ops / (t_async / 1e3) / 1e9, "peak": NOMINAL_FP64_OPS,
             "peak_kind": "nominal FP64 pipe", "traffic": None,
@@ -356,7 +375,8 @@ def run_async_workload(args, local):
            "dtype": "f32/f64" if p.get("f_prec", 64) == 32 else "f64", "data": "synthetic",
            "config": {"workload": WORKLOADS[args.workload], "grid": list(p["n"]), "N": N,
                       "f_steps": p["f_steps"], "tol": p["tol"],
-                      "delay_unit_ns": unit_ns, "delays": delays is not None},
+                      "delay_unit_ns": unit_ns, "delays": delays is not None,
+                      "lazy": bool(args.lazy)},
            "async": {"status": int(code), "time_to_tol_ms": t_async, "kappa": st.iterations,
                      "events": st.events, "cg_iterations": st.cg_iterations,
                      "err_vs_serial_fine": (lam_async - star).abs().max().item() / scale},
@@ -510,7 +530,7 @@ def run_ours(args, world, rank, local):
                 "unit": "GB/s", "traffic": None, "kernel": "step3d<float>",
                 "peak_kind": peak_kind}
     else:
-        ops = FP64_OPS_PER_LUP[dim] * lups_r
+        ops = fp64_ops_per_lup(p) * lups_r
         roof = {"bound": "alu", "achieved": ops / (t_fine / 1e3) / 1e9, "peak": NOMINAL_FP64_OPS,
                 "unit": "Gop/s", "traffic": None,
                 "kernel": ("tri_solve (partition Thomas/PCR)" if dim == 1

@@ -109,6 +109,10 @@ typedef struct pr_async_opts {
   double delay_unit_ns;     /* duration of one delay unit */
   int ctas_per_slice;       /* CTAs cooperating on one slice update (0 = automatic) */
   int quiescence;           /* 1: ignore tol and run until no slice can change */
+  int lazy;                 /* 1: after an update whose fine input was older than its coarse
+                               input, re-update only when a newer predecessor version
+                               appears or the predecessor has settled (skips intermediate
+                               updates that a newer version would supersede) */
 } pr_async_opts;
 
 /* One asynchronous update event (log entry). */

@@ -42,7 +42,7 @@ class pr_async_opts(C.Structure):
     _fields_ = [("paper_literal", C.c_int), ("timeout_s", C.c_double),
                 ("delays_dev", C.c_void_p), ("delay_cols", C.c_int),
                 ("delay_unit_ns", C.c_double), ("ctas_per_slice", C.c_int),
-                ("quiescence", C.c_int)]
+                ("quiescence", C.c_int), ("lazy", C.c_int)]
 
 
 class pr_event(C.Structure):

@@ -52,7 +52,7 @@ struct AsyncDev {
   StencilVar<float> fv32;
   double rtol, tol;
   int maxit;
-  int paper_literal, quiescence;
+  int paper_literal, quiescence, lazy;
   const double* u0;
   // per slice (index i-1)
   double* ring;                   // N * RING * M
@@ -112,10 +112,17 @@ __device__ int freshest_visible(const AsyncDev& a, int j, unsigned long long now
 // visible.  In paper-literal mode it always has work.
 __device__ bool has_work(const AsyncDev& a, int i, unsigned long long now) {
   if (ld_acquire(a.kcount + i - 1) == 0 || a.paper_literal) return true;
-  if (!ld_acquire(a.lastfg + i - 1)) return true;
-  if (i == 1) return false;  // lam_0 = u0 never changes
   int slot = -1;
-  return freshest_visible(a, i - 1, now, &slot) > ld_acquire(a.xver + i - 1);
+  const bool newer = i > 1 && freshest_visible(a, i - 1, now, &slot) > ld_acquire(a.xver + i - 1);
+  if (newer) return true;
+  if (ld_acquire(a.lastfg + i - 1)) return false;  // idempotent: nothing to do
+  if (!a.lazy || i == 1) return true;
+  // lazy: the pending vF == vG update waits until the predecessor has settled
+  // (its own last update idempotent with the latest of its predecessor)
+  const int j = i - 1;
+  const int pred_latest = j == 1 ? 0 : ld_acquire(a.latest + j - 1);
+  return ld_acquire(a.kcount + j - 1) > 0 && ld_acquire(a.lastfg + j - 1) &&
+         ld_acquire(a.xver + j - 1) == pred_latest;
 }
 
 // Stop test of the monitor (any team leader may evaluate it), scanning the
@@ -466,6 +473,7 @@ int run_async(pr_ctx* c, const pr_async_opts* o, double* lam, pr_stats* st, pr_e
   a.maxit = p.g_maxit;
   a.paper_literal = o->paper_literal;
   a.quiescence = o->quiescence;
+  a.lazy = o->lazy;
   a.u0 = p.u0_dev;
   double* dp = static_cast<double*>(c->async_ws);
   a.ring = dp;

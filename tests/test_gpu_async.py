@@ -108,6 +108,20 @@ def test_async_with_injected_delays():
         assert e.t_end >= e.t_start + int(dly * 20000.0) - 1
 
 
+@pytest.mark.parametrize("quiescence", [False, True])
+def test_async_lazy_policy(quiescence):
+    """Skipping superseded re-updates keeps replay parity and the quiescent fixed point."""
+    p = case("heat2d_explicit", tol=1e-9)
+    with Ctx(p) as c:
+        code, st, log, lam = run_async(c, timeout_s=60.0, lazy=True, quiescence=quiescence)
+    assert code == pr.PR_OK and st.converged
+    check_log(log, p["N"])
+    rep = async_replay(p, events_of(log))
+    assert rel_l2(lam, rep.lam) < FP64_TOL
+    if quiescence:
+        assert rel_l2(lam, serial_fine(p)) < FP64_TOL
+
+
 def test_async_paper_literal_mode():
     p = case("heat2d_explicit", tol=1e-9)
     with Ctx(p) as c:
