@@ -17,6 +17,10 @@ One slice [T_{i-1}, T_i] is propagated by (§3.1, definitions of F and G;
   * implicit Euler:  (I + dt A) u_new = u         (fine in 1D, coarse always)
     solved by the Thomas algorithm (1D, exact) or by conjugate gradients
     (2D/3D) stopped when ||r||_2 <= rtol ||b||_2.
+  * trapezoidal rule (Crank-Nicolson), the fine scheme of Table 1:
+      (I + dt/2 A) u_new = (I - dt/2 A) u          (fine, n_f steps)
+    with the right-hand side formed as u - (dt/2) A u, solved by Thomas (1D)
+    or by the same CG (2D/3D) started from the current state u.
 
 Arrays use the layout of ``synthetic.generators``: interior states have
 numpy shape (nx,), (ny, nx) or (nz, ny, nx); kappa has n+2 per axis.
@@ -113,6 +117,30 @@ def implicit_euler_1d(u: np.ndarray, dt: float, h, kappa=None, steps: int = 1) -
     return x
 
 
+def crank_nicolson_1d(u: np.ndarray, dt: float, h, kappa=None, steps: int = 1) -> np.ndarray:
+    """`steps` trapezoidal-rule steps in 1D (§5.1, Table 1's F), Thomas solves."""
+    n = u.shape[-1]
+    sub, diag, sup = tridiagonal_1d(n, 0.5 * dt, h, kappa)
+    x = np.array(u, dtype=np.float64, copy=True)
+    for _ in range(steps):
+        rhs = x - (0.5 * dt) * apply_A(x, h, kappa)
+        x = thomas(sub, diag, sup, rhs)
+    return x
+
+
+def crank_nicolson_cg(u: np.ndarray, dt: float, h, kappa=None, steps: int = 1,
+                      rtol: float = 1e-12, maxit: int = 10000):
+    """`steps` trapezoidal-rule steps in 2D/3D; each solve (I + dt/2 A) x = rhs by
+    the CG below, started from the current state.  Returns (u, total CG iterations)."""
+    x = np.array(u, dtype=np.float64, copy=True)
+    total = 0
+    for _ in range(steps):
+        rhs = x - (0.5 * dt) * apply_A(x, h, kappa)
+        x, it = cg_implicit_euler(rhs, 0.5 * dt, h, kappa, x, rtol, maxit)
+        total += it
+    return x, total
+
+
 def cg_implicit_euler(b: np.ndarray, dt: float, h, kappa=None, x0=None,
                       rtol: float = 1e-10, maxit: int = 10000):
     """One backward-Euler step (I + dt A) x = b by textbook conjugate gradients.
@@ -152,9 +180,10 @@ def cg_implicit_euler(b: np.ndarray, dt: float, h, kappa=None, x0=None,
 class Propagators:
     """F and G of one problem (§3.1): F accurate, G cheap, both over one slice.
 
-    prob keys: dim, n, h, dt (fine step), f_steps, f_scheme ('explicit' or
-    'implicit'), g_solver ('thomas' or 'cg'), g_steps (default 1), g_rtol,
-    g_maxit, kappa.  The coarse step is dT = f_steps * dt.
+    prob keys: dim, n, h, dt (fine step), f_steps, f_scheme ('explicit',
+    'implicit' (1D) or 'cn', the trapezoidal rule), f_rtol/f_maxit (CG of the
+    trapezoidal steps in 2D/3D), g_solver ('thomas' or 'cg'), g_steps
+    (default 1), g_rtol, g_maxit, kappa.  The coarse step is dT = f_steps * dt.
     """
 
     def __init__(self, prob: dict, kappa="from_prob"):
@@ -168,6 +197,8 @@ class Propagators:
         self.g_steps = int(prob.get("g_steps", 1))
         self.g_rtol = float(prob.get("g_rtol", 1e-10))
         self.g_maxit = int(prob.get("g_maxit", 20000))
+        self.f_rtol = float(prob.get("f_rtol") or 1e-12)
+        self.f_maxit = int(prob.get("f_maxit") or 10000)
         self.kappa = prob.get("kappa") if isinstance(kappa, str) else kappa
         self.dT = self.f_steps * self.dt
         self.shape = tuple(reversed(self.n))
@@ -178,6 +209,11 @@ class Propagators:
         x = np.asarray(x, dtype=np.float64).reshape(self.shape)
         if self.f_scheme == "explicit":
             return explicit_euler(x, self.dt, self.h, self.kappa, self.f_steps)
+        if self.f_scheme == "cn":
+            if self.dim == 1:
+                return crank_nicolson_1d(x, self.dt, self.h, self.kappa, self.f_steps)
+            return crank_nicolson_cg(x, self.dt, self.h, self.kappa, self.f_steps,
+                                     self.f_rtol, self.f_maxit)[0]
         if self.dim != 1:
             raise ValueError("implicit fine propagator is 1D (Thomas) only")
         return implicit_euler_1d(x, self.dt, self.h, self.kappa, self.f_steps)

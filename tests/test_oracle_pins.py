@@ -165,6 +165,61 @@ def test_implicit_1d_mode_decay_and_banded():
     np.testing.assert_allclose(x, scipy.linalg.solve_banded((1, 1), ab, b), rtol=1e-12)
 
 
+@pytest.mark.parametrize("n,j", [((13,), (4,)), ((6, 5), (2, 3)), ((4, 3, 5), (3, 2, 1))])
+def test_crank_nicolson_mode_factor(n, j):
+    """Trapezoidal rule on a sine mode: factor (1 - dt mu / 2) / (1 + dt mu / 2) per step,
+    in 1D (Thomas) and 2D/3D (CG), at a step far beyond the explicit limit."""
+    h = tuple(1.0 / (m + 1) for m in n)
+    dt = 3.0 * min(h) ** 2
+    u = sine_mode(n, j, h)
+    mu = sum(4.0 / hh ** 2 * math.sin(jj * math.pi * hh / 2) ** 2 for jj, hh in zip(j, h))
+    fac = ((1 - 0.5 * dt * mu) / (1 + 0.5 * dt * mu)) ** 5
+    if len(n) == 1:
+        out = heat.crank_nicolson_1d(u, dt, h, None, steps=5)
+    else:
+        out, it = heat.crank_nicolson_cg(u, dt, h, None, steps=5, rtol=1e-14)
+        assert it <= 5 * 2   # an eigenvector is solved in one CG iteration (plus rounding)
+    np.testing.assert_allclose(out, fac * u, rtol=1e-11, atol=1e-13)
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_crank_nicolson_variable_kappa_dense(dim):
+    """One trapezoidal step equals (I + dt/2 A)^-1 (I - dt/2 A) u with dense matrices of
+    the flux-form operator (variable kappa); two steps are the square."""
+    n = (9,) if dim == 1 else (5, 4)
+    h = tuple(1.0 / (m + 1) for m in n)
+    shape = tuple(reversed(n))
+    rng = np.random.default_rng(8)
+    kap = np.exp(0.5 * rng.standard_normal(tuple(m + 2 for m in shape)))
+    u = rng.standard_normal(shape)
+    dt = 2.0 * min(h) ** 2
+    A = dense_of(lambda v: heat.apply_A(v, h, kap), shape)
+    I = np.eye(A.shape[0])
+    S = np.linalg.solve(I + 0.5 * dt * A, I - 0.5 * dt * A)
+    if dim == 1:
+        one = heat.crank_nicolson_1d(u, dt, h, kap, steps=1)
+        two = heat.crank_nicolson_1d(u, dt, h, kap, steps=2)
+    else:
+        one, _ = heat.crank_nicolson_cg(u, dt, h, kap, steps=1, rtol=1e-15, maxit=500)
+        two, _ = heat.crank_nicolson_cg(u, dt, h, kap, steps=2, rtol=1e-15, maxit=500)
+    np.testing.assert_allclose(one.reshape(-1), S @ u.reshape(-1), rtol=1e-11, atol=1e-12)
+    np.testing.assert_allclose(two.reshape(-1), S @ S @ u.reshape(-1), rtol=1e-11, atol=1e-12)
+
+
+def test_crank_nicolson_is_second_order_in_time():
+    """Against the exact decay exp(-mu t) of a mode, the error falls ~4x when dt halves
+    (backward Euler would give ~2x): the scheme is the trapezoidal rule."""
+    n, h = (31,), (1 / 32,)
+    u = sine_mode(n, (3,), h)
+    mu = 4.0 / h[0] ** 2 * math.sin(3 * math.pi * h[0] / 2) ** 2
+    T = 4e-3
+    errs = []
+    for steps in (8, 16, 32):
+        out = heat.crank_nicolson_1d(u, T / steps, h, None, steps=steps)
+        errs.append(np.max(np.abs(out - math.exp(-mu * T) * u)))
+    assert 3.6 < errs[0] / errs[1] < 4.4 and 3.6 < errs[1] / errs[2] < 4.4
+
+
 @pytest.mark.parametrize("dim", [2, 3])
 def test_cg_solves_backward_euler(dim):
     n = (5, 4) if dim == 2 else (3, 4, 3)
@@ -207,10 +262,15 @@ def scalar_parareal(f, g, lam0, N, k):
     return out
 
 
-@pytest.mark.parametrize("case", ["1d_implicit", "2d_explicit", "3d_explicit"])
+@pytest.mark.parametrize("case", ["1d_implicit", "2d_explicit", "3d_explicit", "1d_cn", "2d_cn"])
 def test_sync_parareal_matches_closed_form_per_mode(case):
     if case == "1d_implicit":
         prob = small_prob(1, (31,), N=8, f_steps=10, dt_h2=2.0, f_scheme="implicit")
+    elif case == "1d_cn":
+        prob = small_prob(1, (27,), N=7, f_steps=6, dt_h2=3.0, f_scheme="cn")
+    elif case == "2d_cn":
+        prob = small_prob(2, (8, 6), N=5, f_steps=4, dt_h2=2.5, f_scheme="cn")
+        prob["f_rtol"] = 1e-15
     elif case == "2d_explicit":
         prob = small_prob(2, (9, 7), N=6, f_steps=12)
     else:
@@ -220,6 +280,8 @@ def test_sync_parareal_matches_closed_form_per_mode(case):
     mu = grid_mu(n, h)
     if prob["f_scheme"] == "explicit":
         f = (1 - dt * mu) ** prob["f_steps"]
+    elif prob["f_scheme"] == "cn":
+        f = ((1 - 0.5 * dt * mu) / (1 + 0.5 * dt * mu)) ** prob["f_steps"]
     else:
         f = (1 + dt * mu) ** (-prob["f_steps"])
     g = 1.0 / (1 + prob["f_steps"] * dt * mu)
