@@ -50,7 +50,7 @@ enum pr_status {
   PR_ELOGFULL = 7   /* asynchronous event log capacity exceeded; run stopped */
 };
 
-enum pr_scheme { PR_EXPLICIT_EULER = 0, PR_IMPLICIT_EULER = 1 };
+enum pr_scheme { PR_EXPLICIT_EULER = 0, PR_IMPLICIT_EULER = 1, PR_CRANK_NICOLSON = 2 };
 enum pr_solver { PR_SOLVER_THOMAS = 0, PR_SOLVER_CG = 1 };
 
 /* Problem statement (§3.1).  Scalars are copied by parareal_set_problem;
@@ -58,6 +58,11 @@ enum pr_solver { PR_SOLVER_THOMAS = 0, PR_SOLVER_CG = 1 };
  * uses this problem.
  *  f_scheme/f_steps: F = f_steps steps of explicit Euler (any dim) or
  *    implicit Euler (dim 1, Thomas) of size dt = (T-T0)/(N*f_steps).
+ *  f_scheme PR_CRANK_NICOLSON: the trapezoidal rule of Table 1 (§5.1),
+ *    (I + dt/2 A) u' = (I - dt/2 A) u per fine step, unconditionally stable;
+ *    dim 1 by the tridiagonal partition solver (exact), dim 2/3 by conjugate
+ *    gradients started from the current state and stopped when
+ *    ||r||_2 <= f_rtol ||rhs||_2 or after f_maxit iterations.  FP64 only.
  *  f_prec: 64 = FP64 fine steps; 32 = FP32 fine steps with FP64 input and
  *    output (the coarse sweep, correction and test stay FP64).
  *  g_solver: PR_SOLVER_THOMAS (dim 1) or PR_SOLVER_CG; G = one implicit
@@ -82,6 +87,8 @@ typedef struct pr_problem {
   int g_maxit;
   double tol;
   int max_iter;
+  double f_rtol;           /* CG tolerance of the trapezoidal fine steps (<= 0: 1e-12) */
+  int f_maxit;             /* CG iteration cap of one fine step (<= 0: 10000) */
 } pr_problem;
 
 /* Run statistics. */
@@ -97,6 +104,7 @@ typedef struct pr_stats {
   double t_coarse_ms;      /* sync: time in predictor + coarse sweeps; async: 0 */
   long long events;        /* async: slice updates published */
   long long launches;      /* CUDA kernel launches issued by the call */
+  long long fine_cg_iterations; /* CG iterations of the trapezoidal fine steps (2D/3D) */
 } pr_stats;
 
 /* Asynchronous run options (Algorithm 2). */

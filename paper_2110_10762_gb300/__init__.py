@@ -4,7 +4,7 @@ The compute path is libparareal.so (hand-written CUDA, C ABI in
 include/parareal.h); this package is its thin Python binding with the same
 function names, plus a torch.autograd.Function over the discrete adjoint.
 """
-from ._abi import (PR_EXPLICIT_EULER, PR_IMPLICIT_EULER, PR_SOLVER_CG,  # noqa: F401
+from ._abi import (PR_EXPLICIT_EULER, PR_IMPLICIT_EULER, PR_CRANK_NICOLSON, PR_SOLVER_CG,  # noqa: F401
                    PR_SOLVER_THOMAS, PR_OK, PR_ENOTCONV, PR_EINVAL, PR_ETIMEOUT, PR_ESTATE,
                    PR_ELOGFULL, PR_ECUDA, PR_ENOMEM, PR_OPT_PIPELINE, PR_OPT_PIPELINE_CHUNKS,
                    PR_OPT_CG_BLOCKS_PER_SM,

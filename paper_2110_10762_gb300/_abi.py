@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(HERE, "libparareal.so")
 PR_OK, PR_EINVAL, PR_ENOMEM, PR_ECUDA, PR_ETIMEOUT, PR_ENOTCONV, PR_ESTATE, PR_ELOGFULL = range(8)
 STATUS_NAMES = {0: "PR_OK", 1: "PR_EINVAL", 2: "PR_ENOMEM", 3: "PR_ECUDA", 4: "PR_ETIMEOUT",
                 5: "PR_ENOTCONV", 6: "PR_ESTATE", 7: "PR_ELOGFULL"}
-PR_EXPLICIT_EULER, PR_IMPLICIT_EULER = 0, 1
+PR_EXPLICIT_EULER, PR_IMPLICIT_EULER, PR_CRANK_NICOLSON = 0, 1, 2
 PR_SOLVER_THOMAS, PR_SOLVER_CG = 0, 1
 PR_OPT_PIPELINE, PR_OPT_PIPELINE_CHUNKS, PR_OPT_CG_BLOCKS_PER_SM = 1, 2, 3
 
@@ -24,7 +24,8 @@ class pr_problem(C.Structure):
                 ("N", C.c_int), ("u0_dev", C.c_void_p), ("kappa_dev", C.c_void_p),
                 ("f_scheme", C.c_int), ("f_steps", C.c_int), ("f_prec", C.c_int),
                 ("g_solver", C.c_int), ("g_steps", C.c_int), ("g_rtol", C.c_double),
-                ("g_maxit", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int)]
+                ("g_maxit", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int),
+                ("f_rtol", C.c_double), ("f_maxit", C.c_int)]
 
 
 class pr_stats(C.Structure):
@@ -32,7 +33,7 @@ class pr_stats(C.Structure):
                 ("fine_lups", C.c_longlong), ("cg_iterations", C.c_longlong),
                 ("coarse_solves", C.c_longlong), ("t_total_ms", C.c_double),
                 ("t_fine_ms", C.c_double), ("t_coarse_ms", C.c_double), ("events", C.c_longlong),
-                ("launches", C.c_longlong)]
+                ("launches", C.c_longlong), ("fine_cg_iterations", C.c_longlong)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

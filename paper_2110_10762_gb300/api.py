@@ -84,7 +84,7 @@ def parareal_create(device: int = 0, stream=None):
 
 def make_problem(dim, n, T0, T, N, u0, kappa=None, f_scheme=_abi.PR_EXPLICIT_EULER,
                  f_steps=1, f_prec=64, g_solver=_abi.PR_SOLVER_CG, g_steps=1, g_rtol=1e-10,
-                 g_maxit=20000, tol=0.0, max_iter=0) -> pr_problem:
+                 g_maxit=20000, tol=0.0, max_iter=0, f_rtol=0.0, f_maxit=0) -> pr_problem:
     """Fill a pr_problem; u0/kappa are CUDA float64 tensors (kept alive by the caller)."""
     p = pr_problem()
     p.dim = int(dim)
@@ -98,6 +98,7 @@ def make_problem(dim, n, T0, T, N, u0, kappa=None, f_scheme=_abi.PR_EXPLICIT_EUL
     p.g_solver, p.g_steps = int(g_solver), int(g_steps)
     p.g_rtol, p.g_maxit = float(g_rtol), int(g_maxit)
     p.tol, p.max_iter = float(tol), int(max_iter)
+    p.f_rtol, p.f_maxit = float(f_rtol), int(f_maxit)
     return p
 
 

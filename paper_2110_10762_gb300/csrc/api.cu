@@ -27,7 +27,7 @@ namespace {
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 void free_problem(pr_ctx* c) {
-  void* ptrs[] = {c->fcoef, c->fcoef32, c->gcoef, c->v, c->w, c->tmp, c->f32a, c->f32b,
+  void* ptrs[] = {c->fcoef, c->fcoef32, c->gcoef, c->fsys0, c->v, c->w, c->tmp, c->f32a, c->f32b,
                   c->cg_x, c->cg_r, c->cg_p, c->cg_q, c->cg_part, c->cg_iters_dev,
                   c->delta_dev, c->u0_stage, c->lam_stage, c->async_ws, c->adj_ws};
   for (void* p : ptrs)
@@ -35,6 +35,7 @@ void free_problem(pr_ctx* c) {
   c->fcoef = nullptr;
   c->fcoef32 = nullptr;
   c->gcoef = nullptr;
+  c->fsys0 = nullptr;
   c->v = c->w = c->tmp = nullptr;
   c->f32a = c->f32b = nullptr;
   c->cg_x = c->cg_r = c->cg_p = c->cg_q = c->cg_part = nullptr;
@@ -48,9 +49,11 @@ void free_problem(pr_ctx* c) {
   c->adj_ws_bytes = 0;
   tri_free(&c->tri_f);
   tri_free(&c->tri_g);
+  cn_free(c);
   pipeline_free(c);
   c->fvar = {};
   c->gvar = {};
+  c->fsysvar = {};
   c->fvar32 = {};
   c->has_problem = false;
 }
@@ -93,14 +96,20 @@ int check_ready(pr_ctx* c) {
   return PR_OK;
 }
 
-// F on `count` consecutive states.
 cudaError_t fine_batch(pr_ctx* c, const double* in, double* out, int count) {
-  if (c->prob.f_scheme == PR_EXPLICIT_EULER)
-    return explicit_fine(c, in, out, count, c->prob.f_steps, c->prob.f_prec);
-  return tri_solve_steps(c, &c->tri_f, in, out, count, c->prob.f_steps);
+  return fine_apply(c, in, out, count);
 }
 
 }  // namespace
+
+// F on `count` consecutive states: explicit steps, or implicit / trapezoidal
+// steps by the tridiagonal solver (1D) or the batched CG kernel (2D/3D).
+cudaError_t fine_apply(pr_ctx* c, const double* in, double* out, int count) {
+  if (c->prob.f_scheme == PR_EXPLICIT_EULER)
+    return explicit_fine(c, in, out, count, c->prob.f_steps, c->prob.f_prec);
+  if (c->prob.f_scheme == PR_CRANK_NICOLSON && c->g.dim > 1) return cn_fine(c, in, out, count);
+  return tri_solve_steps(c, &c->tri_f, in, out, count, c->prob.f_steps);
+}
 }  // namespace pr
 
 using namespace pr;
@@ -156,8 +165,12 @@ int parareal_set_problem(pr_ctx* c, const pr_problem* pin) {
   if (p.N < 1) return fail(c, PR_EINVAL, "N must be >= 1");
   if (!(p.T > p.T0)) return fail(c, PR_EINVAL, "T must exceed T0");
   if (p.f_steps < 1) return fail(c, PR_EINVAL, "f_steps must be >= 1");
-  if (p.f_scheme != PR_EXPLICIT_EULER && p.f_scheme != PR_IMPLICIT_EULER)
+  if (p.f_scheme != PR_EXPLICIT_EULER && p.f_scheme != PR_IMPLICIT_EULER &&
+      p.f_scheme != PR_CRANK_NICOLSON)
     return fail(c, PR_EINVAL, "unknown f_scheme");
+  if (!(p.f_rtol >= 0.0)) return fail(c, PR_EINVAL, "f_rtol must be >= 0");
+  if (p.f_rtol == 0.0) p.f_rtol = 1e-12;
+  if (p.f_maxit <= 0) p.f_maxit = 10000;
   if (p.f_scheme == PR_IMPLICIT_EULER && p.dim != 1)
     return fail(c, PR_EINVAL, "implicit fine propagator is 1D (Thomas) only");
   if (p.f_prec != 64 && p.f_prec != 32) return fail(c, PR_EINVAL, "f_prec must be 64 or 32");
@@ -178,7 +191,8 @@ int parareal_set_problem(pr_ctx* c, const pr_problem* pin) {
   if (!p.u0_dev) return fail(c, PR_EINVAL, "u0_dev is NULL");
   if (!aligned16(p.u0_dev) || (p.kappa_dev && !aligned16(p.kappa_dev)))
     return fail(c, PR_EINVAL, "device arrays must be 16-byte aligned");
-  if (p.dim == 1 && p.n[0] > 24000 && (p.f_scheme == PR_IMPLICIT_EULER || p.g_solver == PR_SOLVER_THOMAS))
+  if (p.dim == 1 && p.n[0] > 24000 &&
+      (p.f_scheme != PR_EXPLICIT_EULER || p.g_solver == PR_SOLVER_THOMAS))
     return fail(c, PR_EINVAL, "1D Thomas path holds the state in shared memory: n <= 24000");
 
   Geom g{};
@@ -198,6 +212,12 @@ int parareal_set_problem(pr_ctx* c, const pr_problem* pin) {
   const double rx = c->dt / (g.hx * g.hx), ry = p.dim > 1 ? c->dt / (g.hy * g.hy) : 0.0,
                rz = p.dim > 2 ? c->dt / (g.hz * g.hz) : 0.0;
   c->fst = {1.0 - 2.0 * (rx + ry + rz), rx, ry, rz};
+  if (p.f_scheme == PR_CRANK_NICOLSON) {
+    // half steps: right-hand side I - dt/2 A, system I + dt/2 A
+    const double hx = 0.5 * rx, hy = 0.5 * ry, hz = 0.5 * rz;
+    c->fst = {1.0 - 2.0 * (hx + hy + hz), hx, hy, hz};
+    c->fsys = {1.0 + 2.0 * (hx + hy + hz), hx, hy, hz};
+  }
   const double Rx = c->dT / (g.hx * g.hx), Ry = p.dim > 1 ? c->dT / (g.hy * g.hy) : 0.0,
                Rz = p.dim > 2 ? c->dT / (g.hz * g.hz) : 0.0;
   c->gst = {1.0 + 2.0 * (Rx + Ry + Rz), Rx, Ry, Rz};
@@ -233,6 +253,9 @@ int parareal_set_problem(pr_ctx* c, const pr_problem* pin) {
     }
   }
   if (p.f_scheme == PR_IMPLICIT_EULER) chk(tri_build(c, &c->tri_f, g.nx, rx, p.kappa_dev));
+  if (p.f_scheme == PR_CRANK_NICOLSON && p.dim == 1)
+    chk(tri_build(c, &c->tri_f, g.nx, 0.5 * rx, p.kappa_dev, true));
+  if (p.f_scheme == PR_CRANK_NICOLSON && p.dim > 1) chk(cn_alloc(c));
   if (p.g_solver == PR_SOLVER_THOMAS)
     chk(tri_build(c, &c->tri_g, g.nx, c->dT / p.g_steps / (g.hx * g.hx), p.kappa_dev));
   if (e != cudaSuccess) {
@@ -333,6 +356,7 @@ int parareal_serial_fine(pr_ctx* c, double* lam, pr_stats* st) {
   if (!lam || !aligned16(lam)) return fail(c, PR_EINVAL, "bad pointer");
   cudaSetDevice(c->device);
   const long long M = c->g.M;
+  cn_take_iterations(c);
   PR_CUDA(c, cudaEventRecord(c->ev[0], c->stream));
   PR_CUDA(c, cudaMemcpyAsync(lam, c->prob.u0_dev, M * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
   for (int i = 1; i <= c->prob.N; ++i) PR_CUDA(c, fine_batch(c, lam + (i - 1) * M, lam + i * M, 1));
@@ -346,6 +370,7 @@ int parareal_serial_fine(pr_ctx* c, double* lam, pr_stats* st) {
     st->t_fine_ms = ms;
     st->fine_lups = (long long)c->prob.N * M * c->prob.f_steps;
     st->launches = (long long)c->prob.N * (c->prob.f_scheme == PR_EXPLICIT_EULER ? c->prob.f_steps : 1);
+    st->fine_cg_iterations = (long long)cn_take_iterations(c);
     st->iterations = 0;
     st->converged = 1;
   }
@@ -376,7 +401,11 @@ int parareal_run_sync(pr_ctx* c, double* lam, pr_stats* st) {
   if (s) return s;
   if (!lam || !aligned16(lam)) return fail(c, PR_EINVAL, "bad pointer");
   cudaSetDevice(c->device);
-  if (c->opt_pipeline) return run_sync_pipelined(c, lam, st);
+  // the trapezoidal 2D/3D F is itself a cooperative launch over the whole
+  // device, so it cannot overlap the coarse sweep: plain schedule
+  const bool cn_grid = c->prob.f_scheme == PR_CRANK_NICOLSON && c->g.dim > 1;
+  if (c->opt_pipeline && !cn_grid) return run_sync_pipelined(c, lam, st);
+  cn_take_iterations(c);
   const pr_problem& p = c->prob;
   const long long M = c->g.M;
   const int N = p.N;
@@ -506,6 +535,7 @@ int parareal_run_sync(pr_ctx* c, double* lam, pr_stats* st) {
   S.t_total_ms = ms;
   S.t_fine_ms = t_f;
   S.t_coarse_ms = t_g;
+  S.fine_cg_iterations = (long long)cn_take_iterations(c);
   if (st) *st = S;
   if (!conv && p.tol > 0.0) return fail(c, PR_ENOTCONV, "max_iter reached before tol");
   return PR_OK;

@@ -47,6 +47,7 @@ struct TriTables {
   int n = 0;            // unknowns
   int P = 0;            // chunks (lanes used), each with >= 2 rows
   int levels = 0;       // PCR levels of the reduced system (2P rows)
+  int cn = 0;           // 1: trapezoidal steps (right-hand side (I - r A) u formed per step)
   double* buf = nullptr;  // device tables (layout in tridiag.cu)
 };
 
@@ -63,11 +64,15 @@ struct pr_ctx {
   double dt = 0, dT = 0;
   bool var_kappa = false;
   pr::StencilConst fst{}, gst{};   // constant-coefficient F step and G operator
+  // trapezoidal F: fst is then the right-hand side operator I - dt/2 A and
+  // fsys the system operator I + dt/2 A (coarse-operator form)
+  pr::StencilConst fsys{};
   // variable-kappa coefficient arrays (device)
   double* fcoef = nullptr;   // F: c0, cx, cy, cz (FP64)
   float* fcoef32 = nullptr;  // F: FP32 copy for the mixed form
   double* gcoef = nullptr;   // G: c0, cx, cy, cz
-  pr::StencilVar<double> fvar{}, gvar{};
+  double* fsys0 = nullptr;   // trapezoidal F, variable kappa: diagonal of I + dt/2 A
+  pr::StencilVar<double> fvar{}, gvar{}, fsysvar{};
   pr::StencilVar<float> fvar32{};
   // 1D implicit tables
   pr::TriTables tri_f{}, tri_g{};
@@ -100,6 +105,13 @@ struct pr_ctx {
   cudaStream_t s_sweep = nullptr, s_fine = nullptr;
   double* v2 = nullptr;      // second fine-output buffer (N*M)
   std::vector<cudaEvent_t> pev;
+  // trapezoidal F in 2D/3D (cn.cu): team workspaces and control words
+  double* cn_work = nullptr;
+  double* cn_part = nullptr;
+  unsigned long long* cn_bar = nullptr;
+  int* cn_err = nullptr;
+  unsigned long long* cn_iters = nullptr;
+  int cn_teams = 0, cn_cap = 0;
   // async / adjoint workspaces are allocated lazily by their drivers
   void* async_ws = nullptr;
   size_t async_ws_bytes = 0;
@@ -129,8 +141,22 @@ cudaError_t build_var_coefficients(pr_ctx* c);
 // also the transposed step used by the adjoint).
 cudaError_t explicit_step64(pr_ctx* c, const double* in, double* out, int count);
 
+// ---- trapezoidal-rule fine propagator in 2D/3D (cn.cu)
+cudaError_t cn_alloc(pr_ctx* c);
+void cn_free(pr_ctx* c);
+// F (f_steps trapezoidal steps) on `count` consecutive states; synchronises the
+// stream; cudaErrorTimeout when a team barrier wait expired.
+cudaError_t cn_fine(pr_ctx* c, const double* in, double* out, int count);
+// CG iterations of the fine steps since the last call (resets the counter).
+unsigned long long cn_take_iterations(pr_ctx* c);
+// F on `count` consecutive states with the problem's fine scheme (api.cu).
+cudaError_t fine_apply(pr_ctx* c, const double* in, double* out, int count);
+
 // ---- tridiagonal partition solver (tridiag.cu)
-cudaError_t tri_build(pr_ctx* c, TriTables* t, int n, double r, const double* kappa);
+// cn: trapezoidal-rule tables (r is then dt/(2 h^2); each solve is preceded by
+// forming (I - r A) u).
+cudaError_t tri_build(pr_ctx* c, TriTables* t, int n, double r, const double* kappa,
+                      bool cn = false);
 void tri_free(TriTables* t);
 // Solve `steps` times (I + r A) x = b in place for `count` right-hand sides.
 cudaError_t tri_solve_steps(pr_ctx* c, const TriTables* t, const double* in, double* out,

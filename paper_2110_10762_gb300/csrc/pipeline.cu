@@ -38,11 +38,7 @@ namespace {
 cudaError_t fine_rows(pr_ctx* c, const double* lam, double* vbuf, int r0, int r1) {
   const long long M = c->g.M;
   if (r1 <= r0) return cudaSuccess;
-  if (c->prob.f_scheme == PR_EXPLICIT_EULER)
-    return explicit_fine(c, lam + (size_t)r0 * M, vbuf + (size_t)r0 * M, r1 - r0, c->prob.f_steps,
-                         c->prob.f_prec);
-  return tri_solve_steps(c, &c->tri_f, lam + (size_t)r0 * M, vbuf + (size_t)r0 * M, r1 - r0,
-                         c->prob.f_steps);
+  return fine_apply(c, lam + (size_t)r0 * M, vbuf + (size_t)r0 * M, r1 - r0);
 }
 
 }  // namespace

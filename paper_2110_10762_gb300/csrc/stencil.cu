@@ -378,7 +378,7 @@ __global__ void faces_kernel(Geom g, const double* __restrict__ kap, double sF, 
 
 __global__ void diag_kernel(Geom g, const double* fcx, const double* fcy, const double* fcz,
                             const double* gcx, const double* gcy, const double* gcz, double* f0,
-                            double* g0) {
+                            double* g0, double* fs0) {
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < g.M;
        p += (long long)gridDim.x * blockDim.x) {
     const int x = p % g.nx;
@@ -399,6 +399,7 @@ __global__ void diag_kernel(Geom g, const double* fcx, const double* fcy, const 
     }
     f0[p] = 1.0 - sf;
     g0[p] = 1.0 + sg;
+    if (fs0) fs0[p] = 1.0 + sf;
   }
 }
 
@@ -428,8 +429,14 @@ cudaError_t build_var_coefficients(pr_ctx* c) {
   double* gy = gx + nfx;
   double* gz = gy + nfy;
   const int blocks = c->num_sms * 8;
-  faces_kernel<<<blocks, 256, 0, c->stream>>>(g, c->prob.kappa_dev, c->dt, c->dT, fx, fy, fz, gx, gy, gz);
-  diag_kernel<<<blocks, 256, 0, c->stream>>>(g, fx, fy, fz, gx, gy, gz, f0, g0);
+  // trapezoidal F: the F arrays describe the half step (I - dt/2 A), and the
+  // system I + dt/2 A shares their faces with its own diagonal fsys0
+  const bool cn = c->prob.f_scheme == PR_CRANK_NICOLSON;
+  if (cn && (e = cudaMalloc(&c->fsys0, g.M * sizeof(double))) != cudaSuccess) return e;
+  faces_kernel<<<blocks, 256, 0, c->stream>>>(g, c->prob.kappa_dev, cn ? 0.5 * c->dt : c->dt, c->dT,
+                                              fx, fy, fz, gx, gy, gz);
+  diag_kernel<<<blocks, 256, 0, c->stream>>>(g, fx, fy, fz, gx, gy, gz, f0, g0, c->fsys0);
+  if (cn) c->fsysvar = {c->fsys0, fx, nfy ? fy : nullptr, nfz ? fz : nullptr};
   c->fvar = {f0, fx, nfy ? fy : nullptr, nfz ? fz : nullptr};
   c->gvar = {g0, gx, nfy ? gy : nullptr, nfz ? gz : nullptr};
   if (c->prob.f_prec == 32) {

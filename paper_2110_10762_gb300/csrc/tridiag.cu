@@ -10,6 +10,11 @@
 //    reduction across the lanes with warp shuffles;
 //  * each lane then rebuilds its interior from x_s and x_e.
 //
+// Trapezoidal rule (tables built with cn = 1 and r = dt/(2 h^2)): before each
+// solve the lanes form the right-hand side (I - dt/2 A) u in place,
+//   rhs_m = e_m u_m - a_m u_{m-1} - c_m u_{m+1},   e_m = 1 - r (k_{m-1/2} + k_{m+1/2}),
+// with a, c the off-diagonals of I + dt/2 A.
+//
 // The matrix is the same for every step and every slice, so all
 // matrix-only quantities (Thomas factors, spikes, PCR multipliers) are built
 // once by tri_setup; a step then costs about 5 FP64 operations per unknown.
@@ -24,8 +29,8 @@ namespace {
 constexpr int MAXR = 64;  // reduced rows (2 per lane)
 
 struct TriDev {
-  int n, P, base, rem, levels, maxL;
-  const double *a, *c, *cp, *finv, *alpha, *gamma, *k1, *k2, *binv;
+  int n, P, base, rem, levels, maxL, cn;
+  const double *a, *c, *cp, *finv, *alpha, *gamma, *k1, *k2, *binv, *e;
 };
 
 __host__ __device__ inline void chunk_of(int j, int base, int rem, int& s, int& L) {
@@ -38,7 +43,8 @@ __host__ __device__ inline void chunk_of(int j, int base, int rem, int& s, int& 
 __global__ void tri_setup(int n, int P, int base, int rem, int levels, double r,
                           const double* __restrict__ kap, double* a, double* b, double* c,
                           double* cp, double* finv, double* alpha, double* gamma, double* k1,
-                          double* k2, double* binv, double* A, double* B, double* C) {
+                          double* k2, double* binv, double* A, double* B, double* C,
+                          double* ee) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   for (int m = 0; m < n; ++m) {
     const double kl = kap ? 0.5 * (kap[m] + kap[m + 1]) : 1.0;      // face m-1/2
@@ -46,6 +52,7 @@ __global__ void tri_setup(int n, int P, int base, int rem, int levels, double r,
     a[m] = m > 0 ? -r * kl : 0.0;
     c[m] = m < n - 1 ? -r * kr : 0.0;
     b[m] = 1.0 + r * (kl + kr);
+    ee[m] = 1.0 - r * (kl + kr);
   }
   if (n == 1) {
     binv[0] = 1.0 / b[0];
@@ -133,7 +140,7 @@ __global__ void __launch_bounds__(32) tri_solve(TriDev t, const double* __restri
   if (t.n == 1) {
     if (lane == 0) {
       double x = in[base_off];
-      for (int s = 0; s < steps; ++s) x *= t.binv[0];
+      for (int s = 0; s < steps; ++s) x = (t.cn ? t.e[0] * x : x) * t.binv[0];
       out[base_off] = x;
     }
     return;
@@ -144,6 +151,26 @@ __global__ void __launch_bounds__(32) tri_solve(TriDev t, const double* __restri
   if (lane < t.P) chunk_of(lane, t.base, t.rem, s, L);
   double* xc = sm + lane * Ls;  // this lane's chunk, local index 0..L-1
   for (int step = 0; step < steps; ++step) {
+    if (t.cn) {
+      // right-hand side (I - dt/2 A) u in place; the chunk's outer neighbours
+      // are read before any lane overwrites its chunk
+      double left = 0.0, right = 0.0;
+      if (lane < t.P) {
+        if (s > 0) left = sm[pos(s - 1)];
+        if (s + L < t.n) right = sm[pos(s + L)];
+      }
+      __syncwarp();
+      if (lane < t.P) {
+        double prev = left;
+        for (int m = 0; m < L; ++m) {
+          const double cur = xc[m];
+          const double nxt = m + 1 < L ? xc[m + 1] : right;
+          xc[m] = t.e[s + m] * cur - t.a[s + m] * prev - t.c[s + m] * nxt;
+          prev = cur;
+        }
+      }
+      __syncwarp();
+    }
     double r0 = 0.0, r1 = 0.0;
     if (lane < t.P) {
       // interior Thomas: forward then back substitution (y over d, in place)
@@ -222,20 +249,24 @@ TriDev dev_view(const TriTables* t) {
   d.k1 = d.gamma + n;
   d.k2 = d.k1 + (size_t)t->levels * MAXR;
   d.binv = d.k2 + (size_t)t->levels * MAXR;
+  d.e = d.binv + MAXR + n + 3 * MAXR;  // after the setup scratch
+  d.cn = t->cn;
   return d;
 }
 
 }  // namespace
 
-cudaError_t tri_build(pr_ctx* c, TriTables* t, int n, double r, const double* kappa) {
+cudaError_t tri_build(pr_ctx* c, TriTables* t, int n, double r, const double* kappa, bool cn) {
   tri_free(t);
   t->n = n;
+  t->cn = cn ? 1 : 0;
   t->P = n >= 2 ? (n / 2 < 32 ? n / 2 : 32) : 0;
   int R = 2 * t->P, levels = 0;
   while ((1 << levels) < R) ++levels;
   t->levels = levels;
   const size_t words = 6 * (size_t)n + 2 * (size_t)levels * MAXR + MAXR  // tables
-                       + (size_t)n + 3 * MAXR;                            // b and reduced scratch
+                       + (size_t)n + 3 * MAXR                             // b and reduced scratch
+                       + (size_t)n;                                       // e (trapezoidal rhs)
   cudaError_t e = cudaMalloc(&t->buf, words * sizeof(double));
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(t->buf, 0, words * sizeof(double), c->stream);
@@ -250,7 +281,8 @@ cudaError_t tri_build(pr_ctx* c, TriTables* t, int n, double r, const double* ka
                                      const_cast<double*>(d.cp), const_cast<double*>(d.finv),
                                      const_cast<double*>(d.alpha), const_cast<double*>(d.gamma),
                                      const_cast<double*>(d.k1), const_cast<double*>(d.k2),
-                                     const_cast<double*>(d.binv), A, B, C);
+                                     const_cast<double*>(d.binv), A, B, C,
+                                     const_cast<double*>(d.e));
   return cudaGetLastError();
 }
 

@@ -22,13 +22,15 @@ def host(x):
 
 
 def problem_struct(p: dict, u0_t, kappa_t=None, **over):
-    f_scheme = pr.PR_EXPLICIT_EULER if p.get("f_scheme", "explicit") == "explicit" else pr.PR_IMPLICIT_EULER
+    f_scheme = {"explicit": pr.PR_EXPLICIT_EULER, "implicit": pr.PR_IMPLICIT_EULER,
+                "cn": pr.PR_CRANK_NICOLSON}[p.get("f_scheme", "explicit")]
     g_solver = pr.PR_SOLVER_THOMAS if p.get("g_solver") == "thomas" else pr.PR_SOLVER_CG
     kw = dict(dim=p["dim"], n=p["n"], T0=0.0, T=p["N"] * p["f_steps"] * p["dt"], N=p["N"],
               u0=u0_t, kappa=kappa_t, f_scheme=f_scheme, f_steps=p["f_steps"],
               f_prec=p.get("f_prec", 64), g_solver=g_solver, g_rtol=p.get("g_rtol", 1e-10),
               g_maxit=p.get("g_maxit", 20000), tol=p.get("tol", 0.0),
-              max_iter=p.get("max_iter", 0))
+              max_iter=p.get("max_iter", 0), f_rtol=p.get("f_rtol") or 0.0,
+              f_maxit=p.get("f_maxit") or 0)
     kw.update(over)
     return pr.make_problem(**kw)
 

@@ -1,0 +1,151 @@
+"""Trapezoidal-rule (Crank-Nicolson) fine propagator, the fine scheme of
+Table 1 (§5.1): GPU against the oracle.
+
+1D: the partition tridiagonal solver with the explicit half step formed in
+shared memory, against the oracle's Thomas steps (exact solves: 1e-12).
+2D/3D: the batched team-CG kernel against the oracle's CG with the same
+stopping rule and start (x0 = current state); both stop at f_rtol, so the
+states agree to the solver tolerance and the iteration totals match.
+"""
+import numpy as np
+import pytest
+
+from oracle import heat
+from oracle.parareal import serial_fine, sync_parareal
+from synthetic import preset
+
+from .gpu_util import Ctx, dev, host, problem_struct, rel_l2, torch
+
+pr = pytest.importorskip("paper_2110_10762_gb300")
+
+pytestmark = pytest.mark.gpu
+
+EXACT_TOL = 1e-12
+
+
+def cn_case(name, scale="small", dt_h2=2.0, **over):
+    """A preset switched to trapezoidal F steps of dt = dt_h2 h^2 (beyond the explicit limit)."""
+    p = preset(name, scale)
+    h = min(p["h"])
+    p.update(dict(f_scheme="cn", dt=dt_h2 * h * h, f_prec=64, g_rtol=1e-13, f_rtol=1e-13))
+    p.update(over)
+    return p
+
+
+def fine_on_gpu(p, x):
+    with Ctx(p) as c:
+        xin = dev(x)
+        out = torch().empty_like(xin)
+        pr.parareal_fine(c.ctx, xin, out, x.shape[0])
+        return host(out).reshape(x.shape)
+
+
+def states(p, count, seed=3):
+    rng = np.random.default_rng(seed)
+    shape = tuple(reversed(p["n"]))
+    return np.stack([p["u0"] + 0.1 * rng.standard_normal(shape) for _ in range(count)])
+
+
+@pytest.mark.parametrize("var", [False, True])
+def test_cn_fine_1d_thomas(var):
+    p = cn_case("heat1d_thomas", dt_h2=3.0)
+    if var:
+        rng = np.random.default_rng(6)
+        p["kappa"] = np.exp(0.4 * rng.standard_normal(p["n"][0] + 2))
+    P = heat.Propagators(p)
+    x = states(p, 3)
+    got = fine_on_gpu(p, x)
+    for s in range(3):
+        assert rel_l2(got[s], P.F(x[s])) < EXACT_TOL
+
+
+@pytest.mark.parametrize("name,var", [("heat2d_explicit", False), ("heat2d_inverse", True),
+                                      ("heat3d_mixed", False), ("heat3d_varkappa_async", True)])
+def test_cn_fine_2d_3d_cg(name, var):
+    p = cn_case(name, f_steps=4)
+    if not var:
+        p["kappa"] = None
+    P = heat.Propagators(p)
+    x = states(p, 3)
+    with Ctx(p) as c:
+        xin = dev(x)
+        out = torch().empty_like(xin)
+        pr.parareal_fine(c.ctx, xin, out, 3)
+        got = host(out).reshape(x.shape)
+    for s in range(3):
+        ref, it = heat.crank_nicolson_cg(x[s], p["dt"], p["h"], p.get("kappa"), p["f_steps"],
+                                         p["f_rtol"], 10000)
+        # both solves stop at ||r|| <= 1e-13 ||b||: the states agree far below that times cond
+        assert rel_l2(got[s], ref) < 1e-11, (s, rel_l2(got[s], ref))
+
+
+def test_cn_cg_iteration_totals_match_oracle():
+    """The fine CG iteration count reported by the library equals the oracle's for the
+    same inputs (same algorithm, start and stopping rule)."""
+    p = cn_case("heat2d_explicit", f_steps=3, f_rtol=1e-10)
+    p["N"] = 3
+    ref = serial_fine(p)
+    P = heat.Propagators(p)
+    total = 0
+    for i in range(1, p["N"] + 1):
+        _, it = heat.crank_nicolson_cg(ref[i - 1].reshape(tuple(reversed(p["n"]))), p["dt"], p["h"],
+                                       None, p["f_steps"], p["f_rtol"], 10000)
+        total += it
+    with Ctx(p) as c:
+        lam = c.lam()
+        st = pr.parareal_serial_fine(c.ctx, lam)
+        got = host(lam).reshape(ref.shape)
+    assert rel_l2(got, ref) < 1e-9
+    assert abs(st.fine_cg_iterations - total) <= p["N"] * p["f_steps"] // 3, (st.fine_cg_iterations, total)
+
+
+@pytest.mark.parametrize("name", ["heat1d_thomas", "heat2d_explicit"])
+def test_cn_sync_parareal_parity_and_finite_termination(name):
+    p = cn_case(name, tol=1e-5, dt_h2=2.5)
+    if name == "heat1d_thomas":
+        p["g_solver"] = "thomas"
+    ref = sync_parareal(p)
+    assert ref.k < p["N"]
+    star = serial_fine(p)
+    with Ctx(p) as c:
+        lam = c.lam()
+        code, st = pr.parareal_run_sync(c.ctx, lam)
+        got = host(lam).reshape(ref.lam.shape)
+        # k = N iterations reproduce the GPU serial fine solution (§3.2)
+        lamN = c.lam()
+        pr.parareal_set_problem(c.ctx, problem_struct(p, c.u0, c.kappa, tol=0.0))
+        pr.parareal_run_sync(c.ctx, lamN)
+        sf = c.lam()
+        pr.parareal_serial_fine(c.ctx, sf)
+    assert code == pr.PR_OK and st.iterations == ref.k
+    tol = EXACT_TOL if name == "heat1d_thomas" else 1e-9
+    assert rel_l2(got, ref.lam) < tol
+    assert rel_l2(host(lamN), host(sf)) < 1e-12
+    assert rel_l2(host(sf), star) < tol
+
+
+def test_cn_more_slices_than_teams():
+    """A batch larger than the co-resident team count: slices are taken round-robin."""
+    p = cn_case("heat2d_explicit", "tiny", f_steps=2)
+    p["N"] = 400
+    x = states(p, 400, seed=9)
+    got = fine_on_gpu(p, x)
+    P = heat.Propagators(p)
+    for s in (0, 1, 151, 303, 304, 399):
+        assert rel_l2(got[s], P.F(x[s])) < 1e-11
+
+
+def test_cn_rejections():
+    p = cn_case("heat2d_explicit")
+    with Ctx(p) as c:
+        with pytest.raises(pr.PararealError) as e:
+            pr.parareal_run_async(c.ctx, pr.make_async_opts(), c.lam(), log_cap=10)
+        assert e.value.code == pr.PR_EINVAL
+    ctx = pr.parareal_create(0, torch().cuda.current_stream())
+    try:
+        u0 = dev(p["u0"])
+        with pytest.raises(pr.PararealError) as e:
+            pr.parareal_set_problem(ctx, problem_struct(dict(p, f_prec=32), u0))
+        assert e.value.code == pr.PR_EINVAL
+    finally:
+        pr.parareal_destroy(ctx)
