@@ -31,6 +31,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOADS = {
+    "heat2d_cn": "2D heat 512x512, N=32 slices, F=100 trapezoidal-rule (Crank-Nicolson) steps "
+                 "(dt=4h^2, each solved by CG to rtol 1e-12 from the current state), G=1 implicit "
+                 "Euler step by CG (rtol 1e-10), FP64, sync Parareal, tol 1e-6",
+    "heat2d_cn_async": "the 2D heat 512x512 N=32 trapezoidal-F problem (Table 1's F and G) solved "
+                       "by the asynchronous persistent kernel (no injected delays) next to the "
+                       "synchronous solve, tol 1e-6",
     "heat2d_explicit": "2D heat 1024x1024, N=64 slices, F=256 explicit 5-pt steps (dt=0.2h^2), "
                        "G=1 implicit Euler step by CG (rtol 1e-10), FP64, sync Parareal, tol 1e-10",
     "heat3d_mixed": "3D heat 256^3, N=128 slices, F=64 explicit 7-pt steps (dt=0.15h^2), "
@@ -64,6 +70,11 @@ def fp64_ops_per_lup(p, scaled=True):
     return 2.0 * dim + math.ceil(p["f_steps"] / R) / p["f_steps"]
 
 
+# Trapezoidal F in 2D/3D: per CG iteration and point, the operator (1 DMUL + d DADD +
+# d DFMA) plus 5 DFMA (p.q, x, r, r.r, p); per fine step and point, the right-hand side
+# (explicit form, same count as the operator) plus the start residual and its norms (3).
+CN_OPS_PER_CG_POINT = {2: 10, 3: 12}
+CN_OPS_PER_LUP = {2: 13, 3: 17}
 NOMINAL_FP64_OPS = 625.0  # G FP64-pipe ops/s: 1.25 TFLOP/s nominal / 2 flops per DFMA
 # DRAM bytes (read + write) per cell update of the dominant kernel, from one ncu capture
 # of the current kernel; None where no capture of the current kernel exists.
@@ -190,7 +201,7 @@ SIZE_OVERRIDE = {}
 
 def problem_of(name):
     from synthetic import preset
-    base = {"heat2d_async": "heat2d_explicit"}.get(name, name)
+    base = {"heat2d_async": "heat2d_explicit", "heat2d_cn_async": "heat2d_cn"}.get(name, name)
     p = preset(base, "full", **SIZE_OVERRIDE)
     if G_RTOL_OVERRIDE is not None:
         p["g_rtol"] = G_RTOL_OVERRIDE
@@ -201,10 +212,12 @@ def problem_struct(pr, p, u0, kappa=None, **over):
     """pr_problem for a preset dict (T0 = 0, T = N * f_steps * dt)."""
     kw = dict(dim=p["dim"], n=p["n"], T0=0.0, T=p["N"] * p["f_steps"] * p["dt"], N=p["N"],
               u0=u0, kappa=kappa,
-              f_scheme=pr.PR_IMPLICIT_EULER if p.get("f_scheme") == "implicit" else pr.PR_EXPLICIT_EULER,
+              f_scheme={"implicit": pr.PR_IMPLICIT_EULER, "cn": pr.PR_CRANK_NICOLSON}.get(
+                  p.get("f_scheme"), pr.PR_EXPLICIT_EULER),
               f_steps=p["f_steps"], f_prec=p.get("f_prec", 64),
               g_solver=pr.PR_SOLVER_THOMAS if p.get("g_solver") == "thomas" else pr.PR_SOLVER_CG,
-              g_rtol=p.get("g_rtol", 1e-10), tol=p.get("tol", 0.0))
+              g_rtol=p.get("g_rtol", 1e-10), tol=p.get("tol", 0.0),
+              f_rtol=p.get("f_rtol") or 0.0)
     kw.update(over)
     return pr.make_problem(**kw)
 
@@ -228,7 +241,7 @@ def run_reference(args, world, rank):
     if rank != 0:
         return 0
     p = problem_of(args.workload)
-    steps_per_sample = 64 if p["dim"] == 2 else 4
+    steps_per_sample = 8 if p.get("f_scheme") == "cn" else (64 if p["dim"] == 2 else 4)
     for _ in range(args.warmup):
         cpu_sample(p, 1, steps_per_sample)
     tot_t, tot_l = 0.0, 0
@@ -360,8 +373,14 @@ def run_async_workload(args, local):
     lups = sum(r[1].fine_lups for r in res)
     value = lups / (t_async * args.steps / 1e3) / 1e9
     cg_ops = {2: 10.3, 3: 12.3}[p["dim"]]
-    fp64_ops = st.cg_iterations * M * cg_ops + (
-        st.fine_lups * fp64_ops_per_lup(p, scaled=False) if p.get("f_prec", 64) == 64 else 0)
+    if p.get("f_scheme") == "cn":
+        f_ops = (CN_OPS_PER_CG_POINT[p["dim"]] * st.fine_cg_iterations * M
+                 + CN_OPS_PER_LUP[p["dim"]] * st.fine_lups)
+    elif p.get("f_prec", 64) == 64:
+        f_ops = st.fine_lups * fp64_ops_per_lup(p, scaled=False)
+    else:
+        f_ops = 0
+    fp64_ops = st.cg_iterations * M * cg_ops + f_ops
     roof = {"bound": "alu", "kernel": "async_kernel", "unit": "Gop/s",
             "achieved": fp64_ops / (t_async / 1e3) / 1e9, "peak": NOMINAL_FP64_OPS,
             "peak_kind": "nominal FP64 pipe", "traffic": None,
@@ -379,9 +398,11 @@ def run_async_workload(args, local):
                       "lazy": bool(args.lazy)},
            "async": {"status": int(code), "time_to_tol_ms": t_async, "kappa": st.iterations,
                      "events": st.events, "cg_iterations": st.cg_iterations,
+                     "fine_cg_iterations": st.fine_cg_iterations,
                      "err_vs_serial_fine": (lam_async - star).abs().max().item() / scale},
            "sync": {"time_to_tol_ms": t_sync, "k": sst.iterations,
                     "cg_iterations": sst.cg_iterations,
+                    "fine_cg_iterations": sst.fine_cg_iterations,
                     "err_vs_serial_fine": (lam - star).abs().max().item() / scale},
            "async_speedup_vs_sync": t_sync / t_async,
            "kappa_over_k": st.iterations / max(sst.iterations, 1),
@@ -518,9 +539,11 @@ def run_ours(args, world, rank, local):
         pr.parareal_set_option(ctx, pr.PR_OPT_PIPELINE, 1)
     lups_r = sum(s["fine_lups"] for s in roof_stats)
     t_fine = sum(s["t_fine_ms"] for s in roof_stats)
-    # the explicit F is one launch per fine step; the 1D implicit F one launch per batch
+    # the explicit F is one launch per fine step; the 1D implicit F and the
+    # trapezoidal F (one cooperative launch over the batch) one launch per batch
     fine_launches = sum(s["iterations"] for s in roof_stats) * (
-        1 if p.get("f_scheme") == "implicit" else p["f_steps"])
+        1 if p.get("f_scheme") in ("implicit", "cn") else p["f_steps"])
+    is_cn = p.get("f_scheme") == "cn" and dim > 1
     b_elem = 4 if is_mixed else 8
     alg_bytes = 2 * b_elem * lups_r  # one read + one write of the state per step
     hbm_peak, peak_kind = peaks()
@@ -529,6 +552,13 @@ def run_ours(args, world, rank, local):
         roof = {"bound": "hbm", "achieved": alg_bytes / (t_fine / 1e3) / 1e9, "peak": hbm_peak,
                 "unit": "GB/s", "traffic": None, "kernel": "step3d<float>",
                 "peak_kind": peak_kind}
+    elif is_cn:
+        f_its = sum(s["fine_cg_iterations"] for s in roof_stats)
+        ops = CN_OPS_PER_CG_POINT[dim] * f_its * M + CN_OPS_PER_LUP[dim] * lups_r
+        roof = {"bound": "alu", "achieved": ops / (t_fine / 1e3) / 1e9, "peak": NOMINAL_FP64_OPS,
+                "unit": "Gop/s", "traffic": None, "kernel": "cn_kernel (team CG per trapezoidal step)",
+                "peak_kind": "nominal FP64 (1.25 TFLOP/s = 625 G DFMA/s)",
+                "fine_cg_iterations_per_step": f_its / max(lups_r / M, 1)}
     else:
         ops = fp64_ops_per_lup(p) * lups_r
         roof = {"bound": "alu", "achieved": ops / (t_fine / 1e3) / 1e9, "peak": NOMINAL_FP64_OPS,
@@ -590,12 +620,17 @@ def run_ours(args, world, rank, local):
     out["clocks"] = clk.summary()
     pr.parareal_destroy(ctx)
     if rank == 0 and not args.no_cpu:
-        v, dt, l = cpu_sample(p, slices=2 if dim == 2 else 1, steps=None if dim == 2 else 4)
+        if p.get("f_scheme") == "cn":
+            slices, steps = 1, 10
+        elif dim == 2:
+            slices, steps = 2, p["f_steps"]
+        else:
+            slices, steps = 1, 4
+        v, dt, l = cpu_sample(p, slices=slices, steps=steps)
         out["cpu_baseline"] = {"value": v, "unit": "GLUP/s", "cores": 1, "kind": "oracle",
-                               "sample": "oracle F (numpy FP64, single thread) on %s fine "
-                                         "steps of the full grid, %.1f s" % (
-                                             "2 slices x %d" % p["f_steps"] if dim == 2
-                                             else "1 slice x 4", dt)}
+                               "sample": "oracle F (numpy FP64, single thread) on %d slice(s) x "
+                                         "%d fine steps of the full grid, %.1f s" % (
+                                             slices, steps, dt)}
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -615,7 +650,7 @@ def main():
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         return run_reference(args, world, rank)
-    if args.workload in ("heat2d_async", "heat3d_varkappa_async"):
+    if args.workload in ("heat2d_async", "heat3d_varkappa_async", "heat2d_cn_async"):
         return run_async_workload(args, local) if rank == 0 else 0
     if args.workload == "heat2d_inverse":
         return run_adjoint_workload(args, local) if rank == 0 else 0

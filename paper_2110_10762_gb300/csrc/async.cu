@@ -53,6 +53,14 @@ struct AsyncDev {
   double rtol, tol;
   int maxit;
   int paper_literal, quiescence, lazy;
+  // trapezoidal F (2D/3D): right-hand side fst/fv, system fsys/fsv, CG f_rtol/f_maxit
+  int cn;
+  StencilConst fsys;
+  StencilVar<double> fsv;
+  double f_rtol;
+  int f_maxit;
+  int tcg_stride;                 // vectors per team in tcg (4, or 5 with the trapezoidal rhs)
+  unsigned long long* fine_cg;    // CG iterations of the trapezoidal fine steps
   const double* u0;
   // per slice (index i-1)
   double* ring;                   // N * RING * M
@@ -67,7 +75,8 @@ struct AsyncDev {
   int* lastfg;                    // N          last update had vF == vG
   // per team
   double* tv;                     // T * M      fine result v
-  double* tcg;                    // T * 4 * M  CG x, r, p, q (FP64 fine ping-pong aliases r, p)
+  double* tcg;                    // T * tcg_stride * M  CG x, r, p, q (FP64 fine ping-pong aliases
+                                  // r, p), then the trapezoidal right-hand side b
   double* tpart;                  // T * 6 * C
   unsigned long long* bar;        // T      team barrier arrival counters
   int* ctrl;                      // T * 8  (two decision slots, seqlock words)
@@ -157,6 +166,34 @@ __device__ void set_status(const AsyncDev& a, int st) {
   atomicExch(a.stop, 1);
 }
 
+// Trapezoidal fine propagation v = F(xs_i) by the team (Table 1's F): per
+// step the right-hand side b = (I - dt/2 A) u, then (I + dt/2 A) x = b by the
+// team CG from x0 = u; the iterates alternate between ws.x and v so that the
+// last step ends in v.
+__device__ bool team_fine_cn(const AsyncDev& a, const TeamBarrier& bar, const double* xs, double* v,
+                             const CgWork& ws, double* b, int tb) {
+  const Geom& g = a.g;
+  const int S = a.f_steps;
+  const double* src = xs;
+  unsigned long long total = 0;
+  for (int s = 0; s < S; ++s) {
+    double* dst = ((S - 1 - s) % 2 == 0) ? v : ws.x;
+    for_each_point(g, tb, a.C, [&](int x, int y, int z, long long i) {
+      b[i] = fstep_xyz<double, double>(g, a.fst.c0, a.fst.rx, a.fst.ry, a.fst.rz, a.var, a.fv, src,
+                                       x, y, z, i);
+    });
+    if (!bar.sync()) return false;
+    CgWork w2 = ws;
+    w2.x = dst;
+    const int it = cg_core(g, a.fsys, a.var, a.fsv, b, src, a.f_rtol, a.f_maxit, w2, bar, a.C, tb);
+    if (it < 0) return false;
+    total += (unsigned long long)it;
+    src = dst;
+  }
+  if (tb == 0 && threadIdx.x == 0 && total) atomicAdd(a.fine_cg, total);
+  return true;
+}
+
 // Fine propagation v = F(xs_i) by the team: f_steps explicit steps, one team
 // barrier after each.  FP64 steps ping-pong through the CG r/p vectors; FP32
 // steps through the same memory viewed as floats.
@@ -212,7 +249,7 @@ __global__ void __launch_bounds__(ATHREADS) async_kernel(AsyncDev a) {
   TeamBarrier bar{a.bar + team, a.C, deadline + 2000000000ull, a.barrier_err};
   int* ctrl = a.ctrl + 8 * team;
   double* tv = a.tv + (long long)team * M;
-  double* cgx = a.tcg + (long long)team * 4 * M;
+  double* cgx = a.tcg + (long long)team * a.tcg_stride * M;
   CgWork ws{cgx, cgx + M, cgx + 2 * M, cgx + 3 * M, a.tpart + (long long)team * 6 * a.C};
   int cursor = 0;                        // round-robin over owned slices (leader only)
   const int n_own = team < a.N ? (a.N - 1 - team) / a.T + 1 : 0;
@@ -265,8 +302,9 @@ __global__ void __launch_bounds__(ATHREADS) async_kernel(AsyncDev a) {
     if (leader) t_start = globaltimer();
 
     // ---------------- fine propagation v = F(xs_i) ----------------
-    const bool ok = a.f_prec == 32 ? team_fine<float>(a, bar, xs, tv, ws.r, ws.p, tb)
-                                   : team_fine<double>(a, bar, xs, tv, ws.r, ws.p, tb);
+    const bool ok = a.cn ? team_fine_cn(a, bar, xs, tv, ws, cgx + 4 * M, tb)
+                    : a.f_prec == 32 ? team_fine<float>(a, bar, xs, tv, ws.r, ws.p, tb)
+                                     : team_fine<double>(a, bar, xs, tv, ws.r, ws.p, tb);
     if (!ok) break;
 
     // ---------------- freshest visible predecessor version ----------------
@@ -396,6 +434,7 @@ __global__ void async_init(AsyncDev a) {
     *a.status = 0;
     *a.barrier_err = 0;
     *a.log_count = 0ull;
+    *a.fine_cg = 0ull;
   }
   (void)M;
 }
@@ -426,8 +465,11 @@ int async_max_blocks_per_sm() {
 int run_async(pr_ctx* c, const pr_async_opts* o, double* lam, pr_stats* st, pr_event* log_host,
               size_t log_cap, size_t* log_len) {
   const pr_problem& p = c->prob;
-  if (p.f_scheme != PR_EXPLICIT_EULER || p.g_solver != PR_SOLVER_CG)
-    return fail(c, PR_EINVAL, "asynchronous path needs the explicit fine scheme and the CG coarse solver");
+  const bool cn = p.f_scheme == PR_CRANK_NICOLSON;
+  if ((p.f_scheme != PR_EXPLICIT_EULER && !(cn && c->g.dim > 1)) || p.g_solver != PR_SOLVER_CG)
+    return fail(c, PR_EINVAL,
+                "asynchronous path needs the explicit (or, in 2D/3D, trapezoidal) fine scheme and "
+                "the CG coarse solver");
   if (o->timeout_s <= 0.0) return fail(c, PR_EINVAL, "timeout_s must be > 0");
   if (o->delays_dev && o->delay_cols <= 0) return fail(c, PR_EINVAL, "delay_cols must be > 0");
   const long long M = c->g.M;
@@ -440,9 +482,9 @@ int run_async(pr_ctx* c, const pr_async_opts* o, double* lam, pr_stats* st, pr_e
 
   // workspace layout (doubles first, then 8-byte scalars, then ints)
   const size_t d_ring = (size_t)N * RING * M, d_xs = (size_t)N * M, d_tv = (size_t)T * M,
-               d_tcg = (size_t)T * 4 * M, d_tpart = (size_t)T * 6 * C, d_delta = N;
+               d_tcg = (size_t)T * (cn ? 5 : 4) * M, d_tpart = (size_t)T * 6 * C, d_delta = N;
   const size_t n_dbl = d_ring + d_xs + d_tv + d_tcg + d_tpart + d_delta;
-  const size_t n_u64 = (size_t)N * RING + T + 1 + T;  // ring_vis, tdelta, log_count, bar
+  const size_t n_u64 = (size_t)N * RING + T + 1 + T + 1;  // ring_vis, tdelta, log_count, bar, fine_cg
   const size_t n_int = (size_t)N * RING + (N + 1) + 4 * (size_t)N + 2 * (size_t)T + 8 * (size_t)T + 3;
   const size_t bytes = n_dbl * 8 + n_u64 * 8 + n_int * 4 + 256;
   if (c->async_ws_bytes < bytes) {
@@ -474,6 +516,12 @@ int run_async(pr_ctx* c, const pr_async_opts* o, double* lam, pr_stats* st, pr_e
   a.paper_literal = o->paper_literal;
   a.quiescence = o->quiescence;
   a.lazy = o->lazy;
+  a.cn = cn ? 1 : 0;
+  a.fsys = c->fsys;
+  a.fsv = c->fsysvar;
+  a.f_rtol = p.f_rtol;
+  a.f_maxit = p.f_maxit;
+  a.tcg_stride = cn ? 5 : 4;
   a.u0 = p.u0_dev;
   double* dp = static_cast<double*>(c->async_ws);
   a.ring = dp;
@@ -497,6 +545,8 @@ int run_async(pr_ctx* c, const pr_async_opts* o, double* lam, pr_stats* st, pr_e
   up += 1;
   a.bar = up;
   up += T;
+  a.fine_cg = up;
+  up += 1;
   int* ip = reinterpret_cast<int*>(up);
   a.ring_ver = ip;
   ip += (size_t)N * RING;
@@ -567,7 +617,8 @@ int run_async(pr_ctx* c, const pr_async_opts* o, double* lam, pr_stats* st, pr_e
   ++launches;
   PR_CUDA(c, cudaEventRecord(c->ev[3], c->stream));
   int flags[3] = {0, 0, 0};
-  unsigned long long nlog = 0;
+  unsigned long long nlog = 0, fine_cg = 0;
+  PR_CUDA(c, cudaMemcpyAsync(&fine_cg, a.fine_cg, sizeof fine_cg, cudaMemcpyDeviceToHost, c->stream));
   std::vector<int> kc(N);
   std::vector<double> dl(N);
   PR_CUDA(c, cudaMemcpyAsync(flags, a.stop, 3 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -607,6 +658,7 @@ int run_async(pr_ctx* c, const pr_async_opts* o, double* lam, pr_stats* st, pr_e
   S.t_fine_ms = 0;
   S.t_coarse_ms = 0;
   S.launches = launches;
+  S.fine_cg_iterations = (long long)fine_cg;
   const int status = flags[1], berr = flags[2];
   S.converged = (status == AST_OK && !berr) ? 1 : 0;
   if (st) *st = S;

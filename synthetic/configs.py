@@ -35,17 +35,22 @@ PRESETS = {
                                   tol=1e-5, g_rtol=1e-10, f_prec=32, delay_seed=51,
                                   small=dict(n=(29, 24, 21), N=8, f_steps=8),
                                   tiny=dict(n=(4, 3, 3), N=3, f_steps=3)),
+    # trapezoidal-rule F as in Table 1 (dT / dt = 100, eps = 1e-6), steps of 4 h^2
+    "heat2d_cn": dict(dim=2, n=(512, 512), N=32, f_steps=100, f_scheme="cn", g_solver="cg",
+                      dt_h2=4.0, tol=1e-6, g_rtol=1e-10, f_rtol=1e-12, f_prec=64,
+                      small=dict(n=(48, 40), N=6, f_steps=10),
+                      tiny=dict(n=(6, 5), N=4, f_steps=3)),
 }
 
 _U0_SEEDS = {"heat1d_thomas": 1, "heat2d_explicit": 2, "heat3d_mixed": 3,
-             "heat2d_inverse": 4, "heat3d_varkappa_async": 50}
+             "heat2d_inverse": 4, "heat3d_varkappa_async": 50, "heat2d_cn": 6}
 
 
 def _u0(name: str, n) -> np.ndarray:
     seed = _U0_SEEDS[name]
     if name == "heat1d_thomas":
         return gen.sine_modes_1d(n[0], 8, seed)
-    if name in ("heat2d_explicit", "heat2d_inverse"):
+    if name in ("heat2d_explicit", "heat2d_inverse", "heat2d_cn"):
         return gen.modes_and_bumps_2d(n[0], n[1], seed=seed)
     # 3D families: smoothed noise, shape (nz, ny, nx)
     return gen.smoothed_noise_3d((n[2], n[1], n[0]), seed=seed)

@@ -135,8 +135,31 @@ def test_cn_more_slices_than_teams():
         assert rel_l2(got[s], P.F(x[s])) < 1e-11
 
 
+def events_of(log):
+    return [(e.slice, e.version, e.vF, e.vG) for e in log]
+
+
+@pytest.mark.parametrize("quiescence", [False, True])
+def test_cn_async_replay_parity(quiescence):
+    """Asynchronous Parareal with trapezoidal F (Table 1's configuration): the oracle
+    replays the kernel's log with its own trapezoidal F; at quiescence the result is the
+    serial fine solution."""
+    from oracle.parareal import async_replay
+    p = cn_case("heat2d_explicit", tol=1e-8, f_steps=6)
+    with Ctx(p) as c:
+        lam = c.lam()
+        code, st, log = pr.parareal_run_async(
+            c.ctx, pr.make_async_opts(timeout_s=60.0, quiescence=quiescence), lam, log_cap=100000)
+        got = host(lam)
+    assert code == pr.PR_OK and st.converged and st.fine_cg_iterations > 0
+    rep = async_replay(p, events_of(log))
+    assert rel_l2(got, rep.lam) < 1e-11
+    if quiescence:
+        assert rel_l2(got, serial_fine(p)) < 1e-11
+
+
 def test_cn_rejections():
-    p = cn_case("heat2d_explicit")
+    p = cn_case("heat1d_thomas")
     with Ctx(p) as c:
         with pytest.raises(pr.PararealError) as e:
             pr.parareal_run_async(c.ctx, pr.make_async_opts(), c.lam(), log_cap=10)
