@@ -155,6 +155,60 @@ def adjoint_sync(prob: dict, dL_dlamN, K: int, u0=None, kappa="from_prob"):
     return lb[0][0].reshape(ops.shape), gk, lam[K][N].reshape(ops.shape)
 
 
+def adjoint_async(prob: dict, events, dL_dlamN, u0=None, kappa="from_prob"):
+    """Gradients (dL/du0, dL/dkappa) of L(lambda_N) through a logged asynchronous run.
+
+    The run is the one its event log defines (Eq. (12), Algorithm 2; see
+    parareal.async_replay): version 0 of slice i is the predictor value
+    G lambda_{i-1}^0, and event (i, k, vF, vG) makes
+        lambda_i^k = G lambda_{i-1}^{vG} + F lambda_{i-1}^{vF} - G lambda_{i-1}^{vF}
+    (= F lambda_{i-1}^{vF} when vG = vF), the subtracted coarse value being the
+    stored G of the fine input.  lambda_N is slice N's last version.  Reverse
+    mode over that graph: slices N..1 (each version depends only on versions of
+    the previous slice), events of a slice in reverse order, then the
+    predictor chain; with G^T = G and F^T = F,
+        lbar(i-1, vG) += G g,   lbar(i-1, vF) += F g - G g,   g = lbar(i, k).
+    Returns (grad_u0 (state shape), grad_kappa (ring shape) or None, lambda_N).
+    """
+    from .parareal import async_replay
+    ops = _Ops(prob, kappa)
+    if ops.P.f_scheme != "explicit":
+        raise ValueError("adjoint oracle covers the explicit fine propagator")
+    want_k = ops.P.kappa is not None
+    N = int(prob["N"])
+    rep = async_replay(prob, events, u0=u0, kappa=kappa)
+    ver = rep.versions
+    by_slice = {i: [] for i in range(1, N + 1)}
+    for ev in events:
+        i, k, vF, vG = (int(e) for e in ev[:4])
+        by_slice[i].append((k, vF, vG))
+    last = {i: (max(k for k, _, _ in by_slice[i]) if by_slice[i] else 0) for i in range(1, N + 1)}
+    lbar = {key: np.zeros_like(val) for key, val in ver.items()}
+    lbar[(N, last[N])] += np.asarray(dL_dlamN, dtype=np.float64).reshape(-1)
+    gk = np.zeros(ops.ring) if want_k else None
+    for i in range(N, 0, -1):
+        for k, vF, vG in sorted(by_slice[i], reverse=True):
+            g = lbar[(i, k)]
+            if vG > vF:
+                # G's outputs at this event: the new coarse value and the subtracted one
+                z, dk_new = ops.G_adj(ops.G(ver[(i - 1, vG)]), g, want_k)
+                _, dk_old = ops.G_adj(ops.G(ver[(i - 1, vF)]), g, want_k)
+                lbar[(i - 1, vG)] += z
+                lbar[(i - 1, vF)] -= z
+                if want_k:
+                    gk += dk_new - dk_old
+            a, dk = ops.F_adj(ver[(i - 1, vF)], g, want_k)
+            lbar[(i - 1, vF)] += a
+            if want_k:
+                gk += dk
+        # predictor: lambda_i^0 = G lambda_{i-1}^0
+        z, dk = ops.G_adj(ver[(i, 0)], lbar[(i, 0)], want_k)
+        lbar[(i - 1, 0)] += z
+        if want_k:
+            gk += dk
+    return lbar[(0, 0)].reshape(ops.shape), gk, ver[(N, last[N])].reshape(ops.shape)
+
+
 def loss_and_forward(prob: dict, K: int, u_obs, u0=None, kappa="from_prob"):
     """L = 1/2 ||lambda_N^K - u_obs||^2 with K fixed sync iterations (no early stop)."""
     from .parareal import sync_parareal

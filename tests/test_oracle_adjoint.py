@@ -87,3 +87,85 @@ def test_constant_kappa_has_no_kappa_gradient():
     p = prob2d(var=False, seed=8)
     gu0, gk, _ = adjoint_sync(p, np.ones(tuple(reversed(p["n"]))), 2)
     assert gk is None and np.all(np.isfinite(gu0))
+
+
+# ------------------------------------------ adjoint of a logged asynchronous run
+def sync_schedule(N, K):
+    """The synchronous schedule as an event log (each iteration reads the new
+    predecessor for G and the old one for F; slice 1 always reads u0)."""
+    return [(i, k, 0 if i == 1 else k - 1, 0 if i == 1 else k)
+            for k in range(1, K + 1) for i in range(1, N + 1)]
+
+
+def test_async_adjoint_of_sync_schedule_equals_sync_adjoint():
+    """On the synchronous schedule the logged run is the K-iteration Parareal map
+    (Eq. (11); the frozen prefix of Algorithm 1 is the same function), so both adjoints
+    give the same gradients."""
+    from oracle.adjoint import adjoint_async
+    p = prob2d(seed=11, N=4, f_steps=4)
+    K = 3
+    rng = np.random.default_rng(12)
+    g = rng.standard_normal(tuple(reversed(p["n"])))
+    gu_s, gk_s, lam_s = adjoint_sync(p, g, K)
+    gu_a, gk_a, lam_a = adjoint_async(p, sync_schedule(p["N"], K), g)
+    np.testing.assert_allclose(lam_a, lam_s, rtol=0, atol=1e-12 * np.max(np.abs(lam_s)))
+    np.testing.assert_allclose(gu_a, gu_s, rtol=0, atol=1e-10 * np.max(np.abs(gu_s)))
+    np.testing.assert_allclose(gk_a, gk_s, rtol=0, atol=1e-10 * np.max(np.abs(gk_s)))
+
+
+def test_async_adjoint_transposition_identity_random_schedule():
+    """For a fixed log, u0 -> lambda_N is linear: <J v, y> = <v, J^T y>."""
+    from oracle.adjoint import adjoint_async
+    from oracle.parareal import async_replay
+    from .test_oracle_pins import random_schedule
+    p = prob2d(seed=13, N=5, f_steps=3)
+    events = random_schedule(p["N"], np.random.default_rng(14), until_quiescent=False, max_events=23)
+    rng = np.random.default_rng(15)
+    shape = tuple(reversed(p["n"]))
+    v, y = rng.standard_normal(shape), rng.standard_normal(shape)
+    Jv = async_replay(p, events, u0=v).lam[-1]
+    gu0, _, _ = adjoint_async(p, events, y, u0=v)
+    lhs, rhs = float(Jv @ y.reshape(-1)), float(np.sum(v * gu0))
+    assert abs(lhs - rhs) <= 1e-11 * max(abs(lhs), 1.0)
+
+
+def test_async_adjoint_matches_central_differences():
+    from oracle.adjoint import adjoint_async
+    from oracle.parareal import async_replay
+    from .test_oracle_pins import random_schedule
+    p = prob2d(seed=16, N=4, f_steps=3)
+    events = random_schedule(p["N"], np.random.default_rng(17), until_quiescent=False, max_events=15)
+    rng = np.random.default_rng(18)
+    shape = tuple(reversed(p["n"]))
+    u_obs = rng.standard_normal(shape).reshape(-1)
+
+    def loss(kap=None, u0=None):
+        q = dict(p, kappa=p["kappa"] if kap is None else kap)
+        r = async_replay(q, events, u0=u0).lam[-1] - u_obs
+        return 0.5 * float(r @ r), r
+
+    _, r = loss()
+    gu0, gk, _ = adjoint_async(p, events, r)
+    for trial in range(3):
+        d = rng.standard_normal(p["kappa"].shape)
+        eps = 1e-6 * np.max(np.abs(p["kappa"]))
+        fd = (loss(kap=p["kappa"] + eps * d)[0] - loss(kap=p["kappa"] - eps * d)[0]) / (2 * eps)
+        assert np.isclose(np.sum(gk * d), fd, rtol=1e-6, atol=1e-12), (trial, np.sum(gk * d), fd)
+        du = rng.standard_normal(shape)
+        fd = (loss(u0=p["u0"] + 1e-6 * du)[0] - loss(u0=p["u0"] - 1e-6 * du)[0]) / 2e-6
+        assert np.isclose(np.sum(gu0 * du), fd, rtol=1e-6)
+
+
+def test_async_adjoint_at_quiescence_is_adjoint_of_serial_fine():
+    """A quiescent log's result is F^N u0 (Proposition 1), so dL/du0 = F^N g."""
+    from oracle.adjoint import adjoint_async
+    from .test_oracle_pins import random_schedule
+    p = prob2d(seed=19, N=4, f_steps=3)
+    events = random_schedule(p["N"], np.random.default_rng(20))
+    g = np.random.default_rng(21).standard_normal(tuple(reversed(p["n"])))
+    gu0, _, _ = adjoint_async(p, events, g)
+    P = heat.Propagators(p)
+    ref = g
+    for _ in range(p["N"]):
+        ref = P.F(ref)
+    np.testing.assert_allclose(gu0, ref, rtol=0, atol=1e-10 * np.max(np.abs(ref)))
