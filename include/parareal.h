@@ -195,6 +195,26 @@ int parareal_correct(pr_ctx* ctx, const double* w_new_dev, const double* v_dev,
 int parareal_adjoint(pr_ctx* ctx, const double* dL_dlamN_dev, int K, double* grad_u0_dev,
                      double* grad_kappa_dev);
 
+/* Discrete adjoint of a logged asynchronous run (Eq. (12), Algorithm 2): the
+ * event log (host array of n_events pr_event, as written by
+ * parareal_run_async; only slice, version, vF and vG are read) fixes the
+ * computation graph
+ *   lam_i^0 = G lam_{i-1}^0,
+ *   lam_i^k = G lam_{i-1}^{vG} + F lam_{i-1}^{vF} - G lam_{i-1}^{vF}
+ * (= F lam_{i-1}^{vF} when vG = vF), and lam_N = slice N's last version.
+ * The run is replayed on the device keeping every version, then reversed
+ * slice by slice (G and F are symmetric; G taken as the exact solve, CG to
+ * g_rtol).  Given dL/dlam_N (M doubles) writes grad_u0_dev (M doubles),
+ * grad_kappa_dev if non-NULL (prod(n+2) doubles) and, if lamN_dev is
+ * non-NULL, the replayed lam_N (M doubles).  The log may be in any order;
+ * PR_EINVAL when it is not a valid run (versions of a slice not 1, 2, ...;
+ * a fine input other than the previous coarse input; an input version never
+ * produced).  Workspace: (2 V + E) M doubles for V versions and E events,
+ * plus the batched fine states.  FP64 explicit F and CG G only. */
+int parareal_adjoint_async(pr_ctx* ctx, const pr_event* log_host, size_t n_events,
+                           const double* dL_dlamN_dev, double* grad_u0_dev,
+                           double* grad_kappa_dev, double* lamN_dev);
+
 /* Scheduling options (they never change results, only when work runs):
  *  PR_OPT_PIPELINE (0/1, default 0): parareal_run_sync overlaps the fine
  *    propagation of iteration k+1 with the coarse sweep of iteration k (slice

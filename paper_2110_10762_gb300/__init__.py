@@ -10,6 +10,7 @@ from ._abi import (PR_EXPLICIT_EULER, PR_IMPLICIT_EULER, PR_CRANK_NICOLSON, PR_S
                    PR_OPT_CG_BLOCKS_PER_SM,
                    pr_problem, pr_stats, pr_async_opts, pr_event)
 from .api import (PararealError, make_async_opts, make_problem, parareal_adjoint,  # noqa: F401
+                  parareal_adjoint_async,
                   parareal_coarse, parareal_coarse_noalloc, parareal_correct, parareal_create, parareal_destroy,
                   parareal_fine, parareal_last_error, parareal_run_async, parareal_run_sync,
                   parareal_run_sync_host, parareal_serial_fine, parareal_set_problem,

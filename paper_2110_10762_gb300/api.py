@@ -179,6 +179,15 @@ def parareal_adjoint(ctx, dL_dlamN, K: int, grad_u0, grad_kappa=None):
                                                _ptr(grad_kappa)))
 
 
+def parareal_adjoint_async(ctx, log, dL_dlamN, grad_u0, grad_kappa=None, lamN=None):
+    """Adjoint of a logged asynchronous run; `log` is the event list returned by
+    parareal_run_async (pr_event structs) or any sequence of them."""
+    n = len(log)
+    arr = (pr_event * max(n, 1))(*log)
+    return _check(ctx, _lib().parareal_adjoint_async(ctx, arr, n, _ptr(dL_dlamN), _ptr(grad_u0),
+                                                     _ptr(grad_kappa), _ptr(lamN)))
+
+
 def parareal_set_option(ctx, option: int, value: float):
     return _check(ctx, _lib().parareal_set_option(ctx, int(option), float(value)))
 

@@ -19,7 +19,19 @@
 // (a_p - a_q)(u_p - u_q) / (2 h^2) to both of its nodes (boundary ring
 // included); the kernel gathers per node, so it is deterministic and needs
 // no atomics.
+//
+// Adjoint of a logged asynchronous run (Eq. (12), Algorithm 2): the log fixes
+// the computation graph.  Version 0 of slice i is the predictor value
+// G lambda_{i-1}^0; event (i, k, vF, vG) makes
+//   lambda_i^k = G lambda_{i-1}^{vG} + F lambda_{i-1}^{vF} - G lambda_{i-1}^{vF}
+// (= F lambda_{i-1}^{vF} when vG = vF), the subtracted value being the stored
+// coarse value of the fine input.  The forward pass replays the log slice by
+// slice keeping every version; the reverse pass runs slices N..1 (a version
+// depends only on versions of the previous slice): per slice, one CG solve
+// G g per event with vG > vF, the fine adjoints of all its events batched,
+// then the predictor step.
 #include <algorithm>
+#include <map>
 
 #include "device.cuh"
 
@@ -234,6 +246,206 @@ int run_adjoint(pr_ctx* c, const double* gN, int K, double* grad_u0, double* gra
     }
   }
   PR_CUDA(c, cudaMemcpyAsync(grad_u0, L(lb, 0, 0), M * sizeof(double), cudaMemcpyDeviceToDevice,
+                             c->stream));
+  if (grad_kappa)
+    PR_CUDA(c, cudaMemcpyAsync(grad_kappa, kbar, Mr * sizeof(double), cudaMemcpyDeviceToDevice,
+                               c->stream));
+  PR_CUDA(c, cudaStreamSynchronize(c->stream));
+  return PR_OK;
+}
+
+namespace {
+
+struct AEvent {
+  int vF, vG;
+};
+
+__global__ void scatter_add_kernel(double* __restrict__ y, const double* __restrict__ x, double a,
+                                   long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] += a * x[i];
+}
+
+}  // namespace
+
+int run_adjoint_async(pr_ctx* c, const pr_event* log, size_t n_events, const double* gN,
+                      double* grad_u0, double* grad_kappa, double* lamN) {
+  const pr_problem& p = c->prob;
+  if (p.f_scheme != PR_EXPLICIT_EULER || p.g_solver != PR_SOLVER_CG || p.f_prec != 64)
+    return fail(c, PR_EINVAL, "adjoint needs the FP64 explicit fine scheme and the CG coarse solver");
+  const Geom& g = c->g;
+  const long long M = g.M;
+  const int N = p.N, nf = p.f_steps;
+  const bool var = c->var_kappa;
+  if (grad_kappa && !var) return fail(c, PR_EINVAL, "grad_kappa needs a variable-kappa problem");
+  if (n_events && !log) return fail(c, PR_EINVAL, "log is NULL");
+
+  // ---- the graph: events per slice in version order, validated like a replay
+  std::vector<std::vector<AEvent>> ev(N + 1);
+  {
+    std::vector<std::map<int, AEvent>> bys(N + 1);
+    for (size_t e = 0; e < n_events; ++e) {
+      const pr_event& x = log[e];
+      if (x.slice < 1 || x.slice > N || x.version < 1)
+        return fail(c, PR_EINVAL, "log: slice or version out of range");
+      if (!bys[x.slice].emplace(x.version, AEvent{x.vF, x.vG}).second)
+        return fail(c, PR_EINVAL, "log: duplicate (slice, version)");
+    }
+    for (int i = 1; i <= N; ++i) {
+      int expect = 1, prev_vG = 0;
+      for (const auto& kv : bys[i]) {
+        if (kv.first != expect++) return fail(c, PR_EINVAL, "log: versions of a slice not consecutive");
+        const AEvent& a = kv.second;
+        if (a.vF != prev_vG || a.vG < a.vF)
+          return fail(c, PR_EINVAL, "log: fine input is not the previous coarse input");
+        const int pred_max = i == 1 ? 0 : (int)bys[i - 1].size();
+        if (a.vG > pred_max) return fail(c, PR_EINVAL, "log: input version never produced");
+        prev_vG = a.vG;
+        ev[i].push_back(a);
+      }
+    }
+  }
+  // version (i, v) lives at vbase[i] + v; coarse values of events at wbase[i] + k - 1
+  std::vector<size_t> vbase(N + 1), wbase(N + 1);
+  size_t nver = 1, nw = 0;
+  vbase[0] = 0;
+  int kmax = 1;
+  for (int i = 1; i <= N; ++i) {
+    vbase[i] = nver;
+    nver += ev[i].size() + 1;
+    wbase[i] = nw;
+    nw += ev[i].size();
+    kmax = std::max(kmax, (int)ev[i].size());
+  }
+  const int B = std::min(kmax, 16);  // events per batched fine adjoint
+  const long long Mr = ring_count(g);
+  const size_t words = 2 * nver * M + nw * M + (size_t)std::max(nf - 1, 1) * B * M +
+                       3 * (size_t)B * M + M + (var ? (size_t)Mr : 0);
+  const size_t bytes = words * sizeof(double);
+  if (c->adj_ws_bytes < bytes) {
+    if (c->adj_ws) cudaFree(c->adj_ws);
+    c->adj_ws = nullptr;
+    c->adj_ws_bytes = 0;
+    PR_CUDA(c, cudaMalloc(&c->adj_ws, bytes));
+    c->adj_ws_bytes = bytes;
+  }
+  double* ver = static_cast<double*>(c->adj_ws);
+  double* lb = ver + nver * M;
+  double* W = lb + nver * M;
+  double* states = W + nw * M;
+  double* xbuf = states + (size_t)std::max(nf - 1, 1) * B * M;
+  double* abuf0 = xbuf + (size_t)B * M;
+  double* abuf1 = abuf0 + (size_t)B * M;
+  double* zbuf = abuf1 + (size_t)B * M;
+  double* kbar = var ? zbuf + M : nullptr;
+  auto V = [&](double* arr, int i, int v) { return arr + (vbase[i] + v) * M; };
+  const int blocks = c->num_sms * 8;
+  auto axpy = [&](double* y, const double* x, double a, long long n) {
+    axpy_kernel<<<blocks, 256, 0, c->stream>>>(y, x, a, n);
+    return cudaGetLastError();
+  };
+  auto solve = [&](const double* b, const double* x0, double* out) {
+    CgArgs a{};
+    a.b = b;
+    a.x0 = x0;
+    a.out = out;
+    a.iters = c->cg_iters_dev;
+    a.mode = CG_PLAIN;
+    return cg_solve(c, a);
+  };
+  // coarse value subtracted by event k (1-based) of slice i: the last coarse
+  // value produced before it, or the predictor value lambda_i^0
+  auto w_before = [&](int i, int k) -> double* {
+    for (int j = k - 1; j >= 1; --j)
+      if (ev[i][j - 1].vG > ev[i][j - 1].vF) return W + (wbase[i] + j - 1) * M;
+    return V(ver, i, 0);
+  };
+  auto w_after = [&](int i, int k) -> double* {
+    return ev[i][k - 1].vG > ev[i][k - 1].vF ? W + (wbase[i] + k - 1) * M : w_before(i, k);
+  };
+
+  // ------------------------------------------------ forward replay
+  PR_CUDA(c, cudaMemcpyAsync(V(ver, 0, 0), p.u0_dev, M * sizeof(double), cudaMemcpyDeviceToDevice,
+                             c->stream));
+  for (int i = 1; i <= N; ++i) PR_CUDA(c, solve(V(ver, i - 1, 0), V(ver, i - 1, 0), V(ver, i, 0)));
+  unsigned long long* dscratch = c->delta_dev;
+  for (int i = 1; i <= N; ++i) {
+    for (int k = 1; k <= (int)ev[i].size(); ++k) {
+      const AEvent& a = ev[i][k - 1];
+      PR_CUDA(c, fine_apply(c, V(ver, i - 1, a.vF), zbuf, 1));
+      double* wo = w_before(i, k);
+      double* wn = w_after(i, k);
+      if (a.vG > a.vF) PR_CUDA(c, solve(V(ver, i - 1, a.vG), wo, wn));
+      PR_CUDA(c, cudaMemcpyAsync(V(ver, i, k), V(ver, i, k - 1), M * sizeof(double),
+                                 cudaMemcpyDeviceToDevice, c->stream));
+      PR_CUDA(c, correct(c, wn, zbuf, wo, V(ver, i, k), dscratch));
+    }
+  }
+  const int lastN = (int)ev[N].size();
+  if (lamN)
+    PR_CUDA(c, cudaMemcpyAsync(lamN, V(ver, N, lastN), M * sizeof(double), cudaMemcpyDeviceToDevice,
+                               c->stream));
+
+  // ------------------------------------------------------------- reverse
+  PR_CUDA(c, cudaMemsetAsync(lb, 0, nver * M * sizeof(double), c->stream));
+  if (var) PR_CUDA(c, cudaMemsetAsync(kbar, 0, Mr * sizeof(double), c->stream));
+  PR_CUDA(c, axpy(V(lb, N, lastN), gN, 1.0, M));
+  for (int i = N; i >= 1; --i) {
+    const int K = (int)ev[i].size();
+    // coarse terms, one solve per event whose coarse input changed
+    for (int k = K; k >= 1; --k) {
+      const AEvent& a = ev[i][k - 1];
+      if (a.vG == a.vF) continue;
+      PR_CUDA(c, solve(V(lb, i, k), V(lb, i, k), zbuf));
+      PR_CUDA(c, axpy(V(lb, i - 1, a.vG), zbuf, 1.0, M));
+      PR_CUDA(c, axpy(V(lb, i - 1, a.vF), zbuf, -1.0, M));
+      if (var) {
+        facegrad_kernel<<<blocks, 256, 0, c->stream>>>(g, kbar, zbuf, w_after(i, k), 1, -c->dT);
+        facegrad_kernel<<<blocks, 256, 0, c->stream>>>(g, kbar, zbuf, w_before(i, k), 1, c->dT);
+        PR_CUDA(c, cudaGetLastError());
+      }
+    }
+    // fine terms, batched over up to B events: gather inputs and adjoint seeds
+    for (int k0 = 1; k0 <= K; k0 += B) {
+      const int cnt = std::min(B, K - k0 + 1);
+      for (int q = 0; q < cnt; ++q) {
+        const AEvent& a = ev[i][k0 + q - 1];
+        PR_CUDA(c, cudaMemcpyAsync(xbuf + (size_t)q * M, V(ver, i - 1, a.vF), M * sizeof(double),
+                                   cudaMemcpyDeviceToDevice, c->stream));
+        PR_CUDA(c, cudaMemcpyAsync(abuf0 + (size_t)q * M, V(lb, i, k0 + q), M * sizeof(double),
+                                   cudaMemcpyDeviceToDevice, c->stream));
+      }
+      for (int j = 1; j < nf; ++j) {
+        const double* src = j == 1 ? xbuf : states + (size_t)(j - 2) * B * M;
+        PR_CUDA(c, explicit_step64(c, src, states + (size_t)(j - 1) * B * M, cnt));
+      }
+      double* a = abuf0;
+      double* b = abuf1;
+      for (int j = nf - 1; j >= 0; --j) {
+        const double* uj = j == 0 ? xbuf : states + (size_t)(j - 1) * B * M;
+        if (var) {
+          facegrad_kernel<<<blocks, 256, 0, c->stream>>>(g, kbar, a, uj, cnt, -c->dt);
+          PR_CUDA(c, cudaGetLastError());
+        }
+        PR_CUDA(c, explicit_step64(c, a, b, cnt));
+        std::swap(a, b);
+      }
+      for (int q = 0; q < cnt; ++q) {
+        scatter_add_kernel<<<blocks, 256, 0, c->stream>>>(V(lb, i - 1, ev[i][k0 + q - 1].vF),
+                                                          a + (size_t)q * M, 1.0, M);
+        PR_CUDA(c, cudaGetLastError());
+      }
+    }
+    // predictor: lambda_i^0 = G lambda_{i-1}^0
+    PR_CUDA(c, solve(V(lb, i, 0), V(lb, i, 0), zbuf));
+    PR_CUDA(c, axpy(V(lb, i - 1, 0), zbuf, 1.0, M));
+    if (var) {
+      facegrad_kernel<<<blocks, 256, 0, c->stream>>>(g, kbar, zbuf, V(ver, i, 0), 1, -c->dT);
+      PR_CUDA(c, cudaGetLastError());
+    }
+  }
+  PR_CUDA(c, cudaMemcpyAsync(grad_u0, V(lb, 0, 0), M * sizeof(double), cudaMemcpyDeviceToDevice,
                              c->stream));
   if (grad_kappa)
     PR_CUDA(c, cudaMemcpyAsync(grad_kappa, kbar, Mr * sizeof(double), cudaMemcpyDeviceToDevice,

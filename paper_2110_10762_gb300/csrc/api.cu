@@ -595,4 +595,13 @@ int parareal_adjoint(pr_ctx* c, const double* gN, int K, double* grad_u0, double
   return pr::run_adjoint(c, gN, K, grad_u0, grad_kappa);
 }
 
+int parareal_adjoint_async(pr_ctx* c, const pr_event* log, size_t n_events, const double* gN,
+                           double* grad_u0, double* grad_kappa, double* lamN) {
+  int s = check_ready(c);
+  if (s) return s;
+  if (!gN || !grad_u0) return fail(c, PR_EINVAL, "bad pointer");
+  cudaSetDevice(c->device);
+  return pr::run_adjoint_async(c, log, n_events, gN, grad_u0, grad_kappa, lamN);
+}
+
 }  // extern "C"

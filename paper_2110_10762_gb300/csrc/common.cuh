@@ -192,5 +192,7 @@ int run_async(pr_ctx* c, const pr_async_opts* o, double* lam_out, pr_stats* st, 
 
 // ---- adjoint (adjoint.cu)
 int run_adjoint(pr_ctx* c, const double* gN, int K, double* grad_u0, double* grad_kappa);
+int run_adjoint_async(pr_ctx* c, const pr_event* log, size_t n_events, const double* gN,
+                      double* grad_u0, double* grad_kappa, double* lamN);
 
 }  // namespace pr

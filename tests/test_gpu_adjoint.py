@@ -152,3 +152,111 @@ def test_adjoint_rejects_bad_K_and_constant_kappa_gradient():
             pr.parareal_adjoint(c.ctx, gu0, p["N"] + 1, gu0, None)
         with pytest.raises(pr.PararealError):
             pr.parareal_adjoint(c.ctx, gu0, 1, gu0, gu0)   # no kappa to differentiate
+
+
+# ------------------------------------------- adjoint of a logged asynchronous run
+def as_events(tuples):
+    out = []
+    for (i, k, vF, vG) in tuples:
+        e = pr.pr_event()
+        e.slice, e.version, e.vF, e.vG = i, k, vF, vG
+        out.append(e)
+    return out
+
+
+def random_log(N, seed, max_events):
+    """A valid asynchronous schedule (same rule as the oracle's replay tests)."""
+    rng = np.random.default_rng(seed)
+    latest = [0] * (N + 1)
+    last_vG = [0] * (N + 1)
+    last_vF = [0] * (N + 1)
+    events = []
+    for _ in range(max_events):
+        busy = [i for i in range(1, N + 1)
+                if not (last_vF[i] == last_vG[i] == latest[i - 1] and latest[i] > 0)]
+        if not busy:
+            break
+        i = int(rng.choice(busy))
+        vF = last_vG[i]
+        vG = int(rng.integers(vF, latest[i - 1] + 1))
+        latest[i] += 1
+        events.append((i, latest[i], vF, vG))
+        last_vF[i], last_vG[i] = vF, vG
+    return events
+
+
+def gpu_adjoint_async(p, events, g):
+    with Ctx(p) as c:
+        gu0 = torch().empty(c.M, dtype=torch().float64, device="cuda")
+        gk = (torch().empty(p["kappa"].size, dtype=torch().float64, device="cuda")
+              if p.get("kappa") is not None else None)
+        lamN = torch().empty(c.M, dtype=torch().float64, device="cuda")
+        # any order of the log is accepted
+        evs = as_events(events)[::-1]
+        pr.parareal_adjoint_async(c.ctx, evs, dev(g), gu0, gk, lamN)
+        return host(gu0), (host(gk) if gk is not None else None), host(lamN)
+
+
+@pytest.mark.parametrize("name,seed", [("heat2d_inverse", 41), ("heat3d_varkappa_async", 42),
+                                       ("heat2d_explicit", 43)])
+def test_async_adjoint_matches_oracle_random_log(name, seed):
+    from oracle.adjoint import adjoint_async
+    p = small(name)
+    events = random_log(p["N"], seed, max_events=3 * p["N"])
+    g = np.random.default_rng(seed + 1).standard_normal(tuple(reversed(p["n"])))
+    ref_u0, ref_k, ref_lam = adjoint_async(p, events, g)
+    gu0, gk, lamN = gpu_adjoint_async(p, events, g)
+    assert rel_l2(lamN, ref_lam) < 1e-12
+    assert rel_l2(gu0, ref_u0) < ADJ_TOL
+    if ref_k is not None:
+        assert rel_l2(gk, ref_k) < ADJ_TOL
+
+
+def test_async_adjoint_of_sync_schedule_equals_sync_adjoint():
+    """The synchronous schedule written as a log: both GPU adjoints agree."""
+    p = small("heat2d_inverse")
+    K = 3
+    events = [(i, k, 0 if i == 1 else k - 1, 0 if i == 1 else k)
+              for k in range(1, K + 1) for i in range(1, p["N"] + 1)]
+    g = np.random.default_rng(44).standard_normal(tuple(reversed(p["n"])))
+    gu_s, gk_s = gpu_adjoint(p, g, K)
+    gu_a, gk_a, _ = gpu_adjoint_async(p, events, g)
+    assert rel_l2(gu_a, gu_s) < ADJ_TOL
+    assert rel_l2(gk_a, gk_s) < ADJ_TOL
+
+
+def test_async_adjoint_of_a_kernel_log():
+    """The log of a real persistent-kernel run: the replayed lambda_N matches the run's,
+    and the gradients match the oracle's adjoint of the same log."""
+    from oracle.adjoint import adjoint_async
+    p = small("heat2d_inverse", tol=1e-9)
+    with Ctx(p) as c:
+        lam = c.lam()
+        code, st, log = pr.parareal_run_async(c.ctx, pr.make_async_opts(timeout_s=60.0), lam,
+                                              log_cap=100000)
+        run_lamN = host(lam)[p["N"] * c.M:]
+    assert code == pr.PR_OK
+    events = [(e.slice, e.version, e.vF, e.vG) for e in log]
+    g = np.random.default_rng(45).standard_normal(tuple(reversed(p["n"])))
+    gu0, gk, lamN = gpu_adjoint_async(p, events, g)
+    assert rel_l2(lamN, run_lamN) < 1e-11
+    ref_u0, ref_k, _ = adjoint_async(p, events, g)
+    assert rel_l2(gu0, ref_u0) < ADJ_TOL
+    assert rel_l2(gk, ref_k) < ADJ_TOL
+
+
+def test_async_adjoint_rejects_invalid_logs():
+    p = small("heat2d_inverse")
+    g = dev(np.zeros(tuple(reversed(p["n"]))))
+    bad = [
+        [(1, 2, 0, 0)],                      # versions must start at 1
+        [(2, 1, 0, 1)],                      # predecessor version 1 never produced
+        [(1, 1, 0, 0), (2, 1, 0, 1), (2, 2, 0, 1)],  # fine input is not the previous coarse input
+        [(1, 1, 0, 0), (1, 1, 0, 0)],        # duplicate
+    ]
+    with Ctx(p) as c:
+        gu0 = torch().empty(c.M, dtype=torch().float64, device="cuda")
+        for evs in bad:
+            with pytest.raises(pr.PararealError) as e:
+                pr.parareal_adjoint_async(c.ctx, as_events(evs), g, gu0)
+            assert e.value.code == pr.PR_EINVAL
