@@ -34,6 +34,9 @@ WORKLOADS = {
     "heat2d_cn": "2D heat 512x512, N=32 slices, F=100 trapezoidal-rule (Crank-Nicolson) steps "
                  "(dt=4h^2, each solved by CG to rtol 1e-12 from the current state), G=1 implicit "
                  "Euler step by CG (rtol 1e-10), FP64, sync Parareal, tol 1e-6",
+    "heat2d_inverse_async": "2D inverse heat 512x512, variable kappa, N=32, F=128: loss + gradient "
+                            "wrt u0 and kappa through the logged asynchronous run (tol 1e-8) by "
+                            "device replay and reverse pass over the event graph, FP64",
     "heat2d_cn_async": "the 2D heat 512x512 N=32 trapezoidal-F problem (Table 1's F and G) solved "
                        "by the asynchronous persistent kernel (no injected delays) next to the "
                        "synchronous solve, tol 1e-6",
@@ -201,7 +204,8 @@ SIZE_OVERRIDE = {}
 
 def problem_of(name):
     from synthetic import preset
-    base = {"heat2d_async": "heat2d_explicit", "heat2d_cn_async": "heat2d_cn"}.get(name, name)
+    base = {"heat2d_async": "heat2d_explicit", "heat2d_cn_async": "heat2d_cn",
+            "heat2d_inverse_async": "heat2d_inverse"}.get(name, name)
     p = preset(base, "full", **SIZE_OVERRIDE)
     if G_RTOL_OVERRIDE is not None:
         p["g_rtol"] = G_RTOL_OVERRIDE
@@ -468,6 +472,62 @@ def run_adjoint_workload(args, local):
     return 0
 
 
+def run_adjoint_async_workload(args, local):
+    """Gradient of L = 1/2 ||lam_N - u_obs||^2 through a logged asynchronous run."""
+    import numpy as np
+    import torch
+
+    import paper_2110_10762_gb300 as pr
+
+    torch.cuda.set_device(local)
+    p = problem_of(args.workload)
+    N, M, nf = p["N"], int(np.prod(p["n"])), p["f_steps"]
+    u0 = torch.from_numpy(p["u0"].reshape(-1).copy()).cuda()
+    kap = torch.from_numpy(p["kappa"].reshape(-1).copy()).cuda()
+    kstar = torch.from_numpy(p["kappa_star"].reshape(-1).copy()).cuda()
+    ctx = pr.parareal_create(local, torch.cuda.current_stream())
+    pr.parareal_set_problem(ctx, problem_struct(pr, p, u0, kstar))
+    obs = torch.empty((N + 1) * M, dtype=torch.float64, device="cuda")
+    pr.parareal_serial_fine(ctx, obs)
+    u_obs = obs[N * M:].clone()
+    del obs
+    # the logged forward run (async persistent kernel, tol 1e-8)
+    pr.parareal_set_problem(ctx, problem_struct(pr, p, u0, kap, tol=1e-8))
+    lam = torch.empty((N + 1) * M, dtype=torch.float64, device="cuda")
+    code, st, log = pr.parareal_run_async(ctx, pr.make_async_opts(timeout_s=300.0), lam,
+                                          log_cap=1 << 20)
+    gN = lam[N * M:] - u_obs
+    gu = torch.empty(M, dtype=torch.float64, device="cuda")
+    gk = torch.empty(kap.numel(), dtype=torch.float64, device="cuda")
+    lamN = torch.empty(M, dtype=torch.float64, device="cuda")
+
+    def step():
+        pr.parareal_adjoint_async(ctx, log, gN, gu, gk, lamN)
+
+    for _ in range(args.warmup):
+        step()
+    with Clocks(local) as clk:
+        t_ms, _ = _timed(torch, step, args.steps)
+    ups = len(log)
+    coarse = sum(1 for e in log if e.vG > e.vF)
+    # replay F (n_f) + recomputed states (n_f - 1) + transposed steps (n_f) per update
+    lups = ups * M * (3 * nf - 1)
+    out = {"metric": "fine GLUP/s", "value": lups / (t_ms / 1e3) / 1e9, "unit": "GLUP/s",
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": WORKLOADS[args.workload], "grid": list(p["n"]), "N": N,
+                      "f_steps": nf},
+           "forward": {"status": int(code), "kappa": st.iterations, "events": ups,
+                       "coarse_updates": coarse, "t_ms": st.t_total_ms},
+           "replay_vs_run_max_abs": (lamN - lam[N * M:]).abs().max().item(),
+           "grad_u0_norm": gu.norm().item(), "grad_kappa_norm": gk.norm().item(),
+           "gradients_per_s": 1e3 / t_ms, "clocks": clk.summary()}
+    pr.parareal_destroy(ctx)
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -652,6 +712,8 @@ def main():
         return run_reference(args, world, rank)
     if args.workload in ("heat2d_async", "heat3d_varkappa_async", "heat2d_cn_async"):
         return run_async_workload(args, local) if rank == 0 else 0
+    if args.workload == "heat2d_inverse_async":
+        return run_adjoint_async_workload(args, local) if rank == 0 else 0
     if args.workload == "heat2d_inverse":
         return run_adjoint_workload(args, local) if rank == 0 else 0
     return run_ours(args, world, rank, local)
