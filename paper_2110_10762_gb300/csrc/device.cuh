@@ -246,6 +246,115 @@ struct CgWork {
   double* part;  // 2 parity buffers x 3 values x nblk
 };
 
+#ifndef PR_CG_FAST
+#define PR_CG_FAST 1
+#endif
+
+// Operator of the CG passes at one point.  SCALED (constant kappa): k holds
+// {c0/R_x, -, R_y/R_x, R_z/R_x} and the result is (I + dT A) u / R_x, whose x
+// pair needs no multiplier (4 FP64 instructions in 2D, 6 in 3D, against 5 and 7).
+__device__ __forceinline__ double op_point(const Geom& g, const StencilConst& k, bool var,
+                                           bool scaled, const StencilVar<double>& gv,
+                                           const double* __restrict__ u, int x, int y, int z,
+                                           long long idx) {
+  if (var || !scaled) return gop_xyz(g, k, var, gv, u, x, y, z, idx);
+  const long long plane = (long long)g.nx * g.ny;
+  const double w = x > 0 ? u[idx - 1] : 0.0;
+  const double e = x + 1 < g.nx ? u[idx + 1] : 0.0;
+  const double uc = u[idx];
+  double res = fma(k.c0, uc, -(w + e));
+  if (g.dim > 1) {
+    const double s = y > 0 ? u[idx - g.nx] : 0.0;
+    const double n = y + 1 < g.ny ? u[idx + g.nx] : 0.0;
+    res = fma(-k.ry, s + n, res);
+  }
+  if (g.dim > 2) {
+    const double bz = z > 0 ? u[idx - plane] : 0.0;
+    const double fz = z + 1 < g.nz ? u[idx + plane] : 0.0;
+    res = fma(-k.rz, bz + fz, res);
+  }
+  return res;
+}
+
+// q = B p on this block's rows and the partial dot product p.q.  Two warp-rows
+// per trip with p read-only and q write-only (restrict), so the loads of both
+// rows are in flight together instead of one row's latency per trip.
+__device__ __forceinline__ double cg_matvec_dot(const Geom& g, const StencilConst& k, bool var,
+                                                bool scaled, const StencilVar<double>& gv,
+                                                const double* __restrict__ p,
+                                                double* __restrict__ q, int blk, int nblk) {
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  const long long gw = (long long)blk * wpb + (threadIdx.x >> 5);
+  const long long nw = (long long)nblk * wpb;
+  const int xseg = (g.nx + 31) >> 5;
+  const long long items = (long long)g.ny * g.nz * xseg;
+  double sa = 0.0, sb = 0.0;
+  for (long long it = gw; it < items; it += 2 * nw) {
+    const long long itb = it + nw;
+    const long long ra = it / xseg, rb = itb / xseg;
+    const int xa = (int)(it - ra * xseg) * 32 + lane;
+    const int xb = (int)(itb - rb * xseg) * 32 + lane;
+    const bool oka = xa < g.nx;
+    const bool okb = itb < items && xb < g.nx;
+    const long long ia = ra * g.nx + xa, ib = rb * g.nx + xb;
+    double qa = 0.0, qb = 0.0;
+    if (oka) qa = op_point(g, k, var, scaled, gv, p, xa, (int)(ra % g.ny), (int)(ra / g.ny), ia);
+    if (okb) qb = op_point(g, k, var, scaled, gv, p, xb, (int)(rb % g.ny), (int)(rb / g.ny), ib);
+    if (oka) {
+      q[ia] = qa;
+      sa = fma(p[ia], qa, sa);
+    }
+    if (okb) {
+      q[ib] = qb;
+      sb = fma(p[ib], qb, sb);
+    }
+  }
+  return sa + sb;
+}
+
+// x += ax p, r -= ar q over this block's share; returns the partial r.r.
+__device__ __forceinline__ double cg_update_xr(double* __restrict__ x, double* __restrict__ r,
+                                               const double* __restrict__ p,
+                                               const double* __restrict__ q, double ax, double ar,
+                                               long long t0, long long nt, long long M) {
+  double s0 = 0.0, s1 = 0.0;
+  long long i = t0;
+  for (; i + nt < M; i += 2 * nt) {
+    const long long j = i + nt;
+    const double pi = p[i], pj = p[j], qi = q[i], qj = q[j];
+    const double ri = fma(-ar, qi, r[i]);
+    const double rj = fma(-ar, qj, r[j]);
+    x[i] = fma(ax, pi, x[i]);
+    x[j] = fma(ax, pj, x[j]);
+    r[i] = ri;
+    r[j] = rj;
+    s0 = fma(ri, ri, s0);
+    s1 = fma(rj, rj, s1);
+  }
+  if (i < M) {
+    const double ri = fma(-ar, q[i], r[i]);
+    x[i] = fma(ax, p[i], x[i]);
+    r[i] = ri;
+    s0 = fma(ri, ri, s0);
+  }
+  return s0 + s1;
+}
+
+// p = r + beta p over this block's share.
+__device__ __forceinline__ void cg_update_p(double* __restrict__ p, const double* __restrict__ r,
+                                            double beta, long long t0, long long nt, long long M) {
+  long long i = t0;
+  for (; i + nt < M; i += 2 * nt) {
+    const long long j = i + nt;
+    const double pi = fma(beta, p[i], r[i]);
+    const double pj = fma(beta, p[j], r[j]);
+    p[i] = pi;
+    p[j] = pj;
+  }
+  if (i < M) p[i] = fma(beta, p[i], r[i]);
+}
+
 template <class Barrier>
 __device__ int cg_core(const Geom& g, const StencilConst& k, bool var, const StencilVar<double>& gv,
                        const double* __restrict__ b, const double* __restrict__ x0, double rtol,
@@ -278,7 +387,20 @@ __device__ int cg_core(const Geom& g, const StencilConst& k, bool var, const Ste
   const double thresh = rtol * sqrt(bb);
   int it = 0;
   bool done = sqrt(rr) <= thresh || rr == 0.0 || maxit <= 0;
+#if PR_CG_FAST
+  // the passes take the operator scaled by 1/R_x (constant kappa): q' = q / R_x,
+  // so alpha' = rr / p.q' = R_x alpha; r -= alpha' q', x += (alpha' / R_x) p
+  const bool scaled = !var;
+  const StencilConst ks = scaled ? StencilConst{k.c0 / k.rx, 1.0, k.ry / k.rx, k.rz / k.rx} : k;
+  const double sc = scaled ? 1.0 / k.rx : 1.0;
+#endif
   while (!done) {
+#if PR_CG_FAST
+    {
+      const double v[1] = {cg_matvec_dot(g, ks, var, scaled, gv, ws.p, ws.q, blk, nblk)};
+      block_sum<1>(v, part(), blk);
+    }
+#else
     // two accumulators per thread break the dependent FMA chain of the dot product
     double s_a = 0.0, s_b = 0.0;
     for_each_point(g, blk, nblk, [&](int x, int y, int z, long long i) {
@@ -292,11 +414,18 @@ __device__ int cg_core(const Geom& g, const StencilConst& k, bool var, const Ste
       const double v[1] = {s_a + s_b};
       block_sum<1>(v, part(), blk);
     }
+#endif
     if (!bar.sync()) return -1;
     double o1[1];
     group_sum<1>(part(), nblk, o1);
     parity ^= 1;
     const double alpha = rr / o1[0];
+#if PR_CG_FAST
+    {
+      const double v[1] = {cg_update_xr(ws.x, ws.r, ws.p, ws.q, alpha * sc, alpha, t0, nt, M)};
+      block_sum<1>(v, part(), blk);
+    }
+#else
     double s_rn[2] = {0.0, 0.0};
     long long i = t0;
     for (; i + nt < M; i += 2 * nt) {
@@ -320,6 +449,7 @@ __device__ int cg_core(const Geom& g, const StencilConst& k, bool var, const Ste
       const double v[1] = {s_rn[0] + s_rn[1]};
       block_sum<1>(v, part(), blk);
     }
+#endif
     if (!bar.sync()) return -1;
     group_sum<1>(part(), nblk, o1);
     parity ^= 1;
@@ -328,7 +458,11 @@ __device__ int cg_core(const Geom& g, const StencilConst& k, bool var, const Ste
     done = sqrt(rr_new) <= thresh || rr_new == 0.0 || it >= maxit;
     if (!done) {
       const double beta = rr_new / rr;
+#if PR_CG_FAST
+      cg_update_p(ws.p, ws.r, beta, t0, nt, M);
+#else
       for (long long i = t0; i < M; i += nt) ws.p[i] = ws.r[i] + beta * ws.p[i];
+#endif
       rr = rr_new;
       if (!bar.sync()) return -1;
     }
