@@ -177,13 +177,109 @@ def cg_implicit_euler(b: np.ndarray, dt: float, h, kappa=None, x0=None,
     return x, it
 
 
+def coarse_spectrum_bounds(n, h, dt: float, kappa=None):
+    """Interval [a, b] holding the spectrum of I + dt A.
+
+    The eigenvalues of the constant-coefficient A_1 are sums over axes of
+    4/h^2 sin^2(j pi h / 2), j = 1..n (discrete sine modes), so for kappa = 1
+    the bounds are exact.  For variable kappa the Rayleigh quotient
+    <u, A u> = sum_faces kappa_f (Du)_f^2 / h^2 lies between kappa_min and
+    kappa_max (over faces) times that of A_1; the upper bound is also capped by
+    the largest Gershgorin row bound 1 + 2 dt sum_faces kappa_f / h^2.
+    """
+    lo1 = sum(4.0 / hh ** 2 * np.sin(np.pi * hh / 2) ** 2 for hh in h)
+    hi1 = sum(4.0 / hh ** 2 * np.sin(m * np.pi * hh / 2) ** 2 for m, hh in zip(n, h))
+    if kappa is None:
+        return 1.0 + dt * lo1, 1.0 + dt * hi1
+    d = len(n)
+    rows = np.zeros(tuple(reversed(n)))
+    kmin, kmax = np.inf, -np.inf
+    for ax in range(d):
+        inner = [slice(1, -1)] * d
+        inner[ax] = slice(None)
+        K = kappa[tuple(inner)]
+        hi_ = [slice(None)] * d
+        lo_ = [slice(None)] * d
+        hi_[ax] = slice(1, None)
+        lo_[ax] = slice(None, -1)
+        kf = 0.5 * (K[tuple(hi_)] + K[tuple(lo_)])        # n+1 faces along ax
+        kmin, kmax = min(kmin, float(kf.min())), max(kmax, float(kf.max()))
+        a = [slice(None)] * d
+        b = [slice(None)] * d
+        a[ax] = slice(None, -1)
+        b[ax] = slice(1, None)
+        rows = rows + (kf[tuple(a)] + kf[tuple(b)]) / _h_of_axis(h, d, ax) ** 2
+    gersh = 1.0 + 2.0 * dt * float(rows.max())
+    return 1.0 + dt * kmin * lo1, min(gersh, 1.0 + dt * kmax * hi1)
+
+
+def chebyshev_apply(op, f: np.ndarray, m: int, a: float, b: float) -> np.ndarray:
+    """m steps of Chebyshev iteration for op(y) = f from y = 0 on the interval
+    [a, b] (three-term recurrence of Chebyshev acceleration): a fixed
+    polynomial p_m(B) f with residual polynomial T_m((c - x)/e) / T_m(c/e),
+    c = (a+b)/2, e = (b-a)/2, used as the preconditioner z = p_m(B) r."""
+    c, e = 0.5 * (b + a), 0.5 * (b - a)
+    sigma = c / e
+    rho = 1.0 / sigma
+    res = np.array(f, dtype=np.float64, copy=True)
+    d = res / c
+    y = d.copy()
+    for _ in range(1, m):
+        res = res - op(d)
+        rho_new = 1.0 / (2.0 * sigma - rho)
+        d = (rho_new * rho) * d + (2.0 * rho_new / e) * res
+        y = y + d
+        rho = rho_new
+    return y
+
+
+def pcg_implicit_euler(b: np.ndarray, dt: float, h, kappa=None, x0=None, rtol: float = 1e-10,
+                       maxit: int = 10000, m: int = 8, bounds=None):
+    """(I + dt A) x = b by preconditioned conjugate gradients with the degree-m
+    Chebyshev polynomial preconditioner above (spectrum bounds from
+    coarse_spectrum_bounds unless given).  Same start and stopping rule as
+    cg_implicit_euler.  Returns (x, iters)."""
+    b = np.asarray(b, dtype=np.float64)
+    x = np.array(b if x0 is None else x0, dtype=np.float64, copy=True)
+    n = tuple(reversed(b.shape))
+
+    def op(v):
+        return v + dt * apply_A(v, h, kappa)
+
+    lo, hi = bounds if bounds is not None else coarse_spectrum_bounds(n, h, dt, kappa)
+    bnorm = np.sqrt(np.sum(b * b))
+    r = b - op(x)
+    rr = np.sum(r * r)
+    it = 0
+    if np.sqrt(rr) <= rtol * bnorm or rr == 0.0:
+        return x, it
+    z = chebyshev_apply(op, r, m, lo, hi)
+    rz = np.sum(r * z)
+    p = z.copy()
+    while it < maxit:
+        q = op(p)
+        alpha = rz / np.sum(p * q)
+        x = x + alpha * p
+        r = r - alpha * q
+        rr = np.sum(r * r)
+        it += 1
+        if np.sqrt(rr) <= rtol * bnorm or rr == 0.0:
+            break
+        z = chebyshev_apply(op, r, m, lo, hi)
+        rz_new = np.sum(r * z)
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return x, it
+
+
 class Propagators:
     """F and G of one problem (§3.1): F accurate, G cheap, both over one slice.
 
     prob keys: dim, n, h, dt (fine step), f_steps, f_scheme ('explicit',
     'implicit' (1D) or 'cn', the trapezoidal rule), f_rtol/f_maxit (CG of the
     trapezoidal steps in 2D/3D), g_solver ('thomas' or 'cg'), g_steps
-    (default 1), g_rtol, g_maxit, kappa.  The coarse step is dT = f_steps * dt.
+    (default 1), g_rtol, g_maxit, g_cheb (0: plain CG; m >= 2: CG preconditioned
+    by m Chebyshev steps), kappa.  The coarse step is dT = f_steps * dt.
     """
 
     def __init__(self, prob: dict, kappa="from_prob"):
@@ -197,6 +293,7 @@ class Propagators:
         self.g_steps = int(prob.get("g_steps", 1))
         self.g_rtol = float(prob.get("g_rtol", 1e-10))
         self.g_maxit = int(prob.get("g_maxit", 20000))
+        self.g_cheb = int(prob.get("g_cheb") or 0)
         self.f_rtol = float(prob.get("f_rtol") or 1e-12)
         self.f_maxit = int(prob.get("f_maxit") or 10000)
         self.kappa = prob.get("kappa") if isinstance(kappa, str) else kappa
@@ -227,4 +324,7 @@ class Propagators:
                 raise ValueError("Thomas coarse propagator is 1D only")
             return implicit_euler_1d(x, dTg, self.h, self.kappa, self.g_steps), 0
         x0 = None if x0 is None else np.asarray(x0, dtype=np.float64).reshape(self.shape)
+        if self.g_cheb:
+            return pcg_implicit_euler(x, dTg, self.h, self.kappa, x0, self.g_rtol, self.g_maxit,
+                                      self.g_cheb)
         return cg_implicit_euler(x, dTg, self.h, self.kappa, x0, self.g_rtol, self.g_maxit)

@@ -240,6 +240,69 @@ def test_cg_solves_backward_euler(dim):
     np.testing.assert_allclose(xm, u / (1 + dT * mu), rtol=1e-12, atol=1e-14)
 
 
+@pytest.mark.parametrize("m", [2, 5, 8])
+def test_chebyshev_preconditioner_on_a_mode(m):
+    """On an eigenvector of B = I + dT A with eigenvalue lam, m Chebyshev steps give
+    (1 - T_m((c - lam)/e) / T_m(c/e)) / lam times the vector (c, e: centre and half
+    width of the bounds)."""
+    n, j = (7, 6), (3, 2)
+    h = tuple(1.0 / (k + 1) for k in n)
+    dT = 30 * min(h) ** 2
+    u = sine_mode(n, j, h)
+    mu = sum(4.0 / hh ** 2 * math.sin(jj * math.pi * hh / 2) ** 2 for jj, hh in zip(j, h))
+    lam = 1 + dT * mu
+    a, b = heat.coarse_spectrum_bounds(n, h, dT)
+    c, e = (a + b) / 2, (b - a) / 2
+    T = lambda k, x: np.cosh(k * np.arccosh(x)) if abs(x) >= 1 else np.cos(k * np.arccos(x))
+    fac = (1 - T(m, (c - lam) / e) / T(m, c / e)) / lam
+    op = lambda v: v + dT * heat.apply_A(v, h, None)
+    np.testing.assert_allclose(heat.chebyshev_apply(op, u, m, a, b), fac * u, rtol=1e-11, atol=1e-14)
+
+
+@pytest.mark.parametrize("var", [False, True])
+def test_coarse_spectrum_bounds(var):
+    """Constant kappa: the bounds are the extreme eigenvalues; variable kappa: they
+    enclose the spectrum (dense eigenvalues)."""
+    n = (6, 5)
+    h = tuple(1.0 / (k + 1) for k in n)
+    shape = tuple(reversed(n))
+    rng = np.random.default_rng(22)
+    kap = np.exp(0.5 * rng.standard_normal(tuple(k + 2 for k in shape))) if var else None
+    dT = 25 * min(h) ** 2
+    D = dense_of(lambda v: v + dT * heat.apply_A(v, h, kap), shape)
+    ev = np.linalg.eigvalsh(0.5 * (D + D.T))
+    a, b = heat.coarse_spectrum_bounds(n, h, dT, kap)
+    if var:
+        assert a <= ev.min() + 1e-12 and ev.max() <= b + 1e-12
+    else:
+        np.testing.assert_allclose([a, b], [ev.min(), ev.max()], rtol=1e-12)
+
+
+@pytest.mark.parametrize("var", [False, True])
+def test_pcg_solves_backward_euler(var):
+    n = (7, 5)
+    h = tuple(1.0 / (k + 1) for k in n)
+    shape = tuple(reversed(n))
+    rng = np.random.default_rng(23)
+    kap = np.exp(0.5 * rng.standard_normal(tuple(k + 2 for k in shape))) if var else None
+    b = rng.standard_normal(shape)
+    dT = 60 * min(h) ** 2
+    D = dense_of(lambda v: v + dT * heat.apply_A(v, h, kap), shape)
+    x, it = heat.pcg_implicit_euler(b, dT, h, kap, None, rtol=1e-14, maxit=500, m=6)
+    np.testing.assert_allclose(x.reshape(-1), np.linalg.solve(D, b.reshape(-1)), rtol=1e-11, atol=1e-12)
+    # on a grid large enough for CG to be far from finite termination, the
+    # preconditioner cuts the iteration count
+    n = (40, 30)
+    h = tuple(1.0 / (k + 1) for k in n)
+    shape = tuple(reversed(n))
+    kap = np.exp(0.5 * rng.standard_normal(tuple(k + 2 for k in shape))) if var else None
+    b = rng.standard_normal(shape)
+    dT = 60 * min(h) ** 2
+    _, it = heat.pcg_implicit_euler(b, dT, h, kap, None, rtol=1e-10, maxit=500, m=6)
+    _, it_cg = heat.cg_implicit_euler(b, dT, h, kap, None, rtol=1e-10, maxit=500)
+    assert it < 0.8 * it_cg, (it, it_cg)
+
+
 def test_cg_zero_rhs_and_warm_start():
     h = (1 / 6, 1 / 6)
     x, it = heat.cg_implicit_euler(np.zeros((5, 5)), 0.1, h)
@@ -262,7 +325,8 @@ def scalar_parareal(f, g, lam0, N, k):
     return out
 
 
-@pytest.mark.parametrize("case", ["1d_implicit", "2d_explicit", "3d_explicit", "1d_cn", "2d_cn"])
+@pytest.mark.parametrize("case", ["1d_implicit", "2d_explicit", "3d_explicit", "1d_cn", "2d_cn",
+                                  "2d_explicit_pcg"])
 def test_sync_parareal_matches_closed_form_per_mode(case):
     if case == "1d_implicit":
         prob = small_prob(1, (31,), N=8, f_steps=10, dt_h2=2.0, f_scheme="implicit")
@@ -273,6 +337,9 @@ def test_sync_parareal_matches_closed_form_per_mode(case):
         prob["f_rtol"] = 1e-15
     elif case == "2d_explicit":
         prob = small_prob(2, (9, 7), N=6, f_steps=12)
+    elif case == "2d_explicit_pcg":
+        prob = small_prob(2, (9, 7), N=6, f_steps=12)
+        prob["g_cheb"] = 4
     else:
         prob = small_prob(3, (5, 4, 6), N=5, f_steps=8, dt_h2=0.15)
     n, h, N = prob["n"], prob["h"], prob["N"]
