@@ -104,6 +104,8 @@ def parse():
     ap.add_argument("--pipeline", action="store_true",
                     help="overlap F of iteration k+1 with the coarse sweep of iteration k")
     ap.add_argument("--chunks", type=int, default=8, help="slice chunks per pipelined F batch")
+    ap.add_argument("--g-cheb", type=int, default=0,
+                    help="coarse CG preconditioned by this many FP32 Chebyshev steps (0 = plain CG)")
     ap.add_argument("--lazy", action="store_true",
                     help="async workloads: skip re-updates that a newer input will supersede")
     ap.add_argument("--cg-bps", type=int, default=0,
@@ -554,6 +556,8 @@ def run_ours(args, world, rank, local):
         pr.parareal_set_option(ctx, pr.PR_OPT_PIPELINE, 1)
         pr.parareal_set_option(ctx, pr.PR_OPT_PIPELINE_CHUNKS, args.chunks)
         pr.parareal_set_option(ctx, pr.PR_OPT_CG_BLOCKS_PER_SM, args.cg_bps)
+    if args.g_cheb:
+        pr.parareal_set_option(ctx, pr.PR_OPT_G_CHEBYSHEV, args.g_cheb)
     lam = torch.empty((N + 1) * M, dtype=torch.float64, device="cuda")
     if args.profile:
         code, st = pr.parareal_run_sync(ctx, lam)
@@ -643,6 +647,8 @@ def run_ours(args, world, rank, local):
                       "parallelism": "replicas" if world > 1 else "1 GPU",
                       "schedule": ("pipelined (F of k+1 overlaps the sweep of k)"
                                    if args.pipeline else "plain"),
+                      "coarse_solver": ("CG preconditioned by %d FP32 Chebyshev steps" % args.g_cheb
+                                        if args.g_cheb else "CG"),
                       "l2": "inputs larger than L2 (trajectory %.2f GB + workspaces)" % (
                           (N + 1) * M * 8 / 1e9)},
            "iterations": stats[-1]["iterations"], "time_to_tol_ms": ms / args.steps,

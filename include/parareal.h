@@ -224,8 +224,23 @@ int parareal_adjoint_async(pr_ctx* ctx, const pr_event* log_host, size_t n_event
  *    identical to the plain schedule.  Needs N*M more doubles.
  *  PR_OPT_PIPELINE_CHUNKS (1..1024, default 8): slice chunks per fine batch.
  *  PR_OPT_CG_BLOCKS_PER_SM (0 = automatic): cap on the co-resident blocks per
- *    SM of the coarse CG kernel (leaves room for concurrent fine work). */
-enum pr_option { PR_OPT_PIPELINE = 1, PR_OPT_PIPELINE_CHUNKS = 2, PR_OPT_CG_BLOCKS_PER_SM = 3 };
+ *    SM of the coarse CG kernel (leaves room for concurrent fine work).
+ * and one that changes the coarse solver (not its stopping rule):
+ *  PR_OPT_G_CHEBYSHEV (0 = plain CG, default; m in [2, 64]): the coarse CG
+ *    of the synchronous driver, the predictor and the adjoint is
+ *    preconditioned by m steps of Chebyshev iteration on the spectrum bounds
+ *    of I + dT A (exact for kappa = 1, Rayleigh/Gershgorin bounds otherwise),
+ *    computed in FP32; the CG recurrences and the test ||r||_2 <= g_rtol
+ *    ||b||_2 stay FP64, so the result meets the same residual bound (and,
+ *    I + dT A >= I, lies within 2 g_rtol ||b||_2 of the plain CG result).
+ *    Needs M doubles and 4 M floats more.  The asynchronous kernel keeps plain
+ *    CG. */
+enum pr_option {
+  PR_OPT_PIPELINE = 1,
+  PR_OPT_PIPELINE_CHUNKS = 2,
+  PR_OPT_CG_BLOCKS_PER_SM = 3,
+  PR_OPT_G_CHEBYSHEV = 4
+};
 int parareal_set_option(pr_ctx* ctx, int option, double value);
 
 /* Per-slice statistics of the last run (host arrays of N entries, may be NULL):

@@ -16,7 +16,7 @@ STATUS_NAMES = {0: "PR_OK", 1: "PR_EINVAL", 2: "PR_ENOMEM", 3: "PR_ECUDA", 4: "P
                 5: "PR_ENOTCONV", 6: "PR_ESTATE", 7: "PR_ELOGFULL"}
 PR_EXPLICIT_EULER, PR_IMPLICIT_EULER, PR_CRANK_NICOLSON = 0, 1, 2
 PR_SOLVER_THOMAS, PR_SOLVER_CG = 0, 1
-PR_OPT_PIPELINE, PR_OPT_PIPELINE_CHUNKS, PR_OPT_CG_BLOCKS_PER_SM = 1, 2, 3
+PR_OPT_PIPELINE, PR_OPT_PIPELINE_CHUNKS, PR_OPT_CG_BLOCKS_PER_SM, PR_OPT_G_CHEBYSHEV = 1, 2, 3, 4
 
 
 class pr_problem(C.Structure):

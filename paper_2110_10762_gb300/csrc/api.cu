@@ -50,6 +50,7 @@ void free_problem(pr_ctx* c) {
   tri_free(&c->tri_f);
   tri_free(&c->tri_g);
   cn_free(c);
+  cheb_free(c);
   pipeline_free(c);
   c->fvar = {};
   c->gvar = {};
@@ -262,6 +263,12 @@ int parareal_set_problem(pr_ctx* c, const pr_problem* pin) {
     free_problem(c);
     return cuda_fail(c, e, "tridiagonal tables");
   }
+  if (p.g_solver == PR_SOLVER_CG) chk(coarse_bounds(c));
+  if (p.g_solver == PR_SOLVER_CG && c->opt_g_cheb) chk(cheb_alloc(c));
+  if (e != cudaSuccess) {
+    free_problem(c);
+    return cuda_fail(c, e, "coarse preconditioner");
+  }
   // Stability of the explicit step: dt * lambda_max(A) <= 2 (exact for constant
   // kappa; Gershgorin bound, i.e. every diagonal c0 >= 0, for variable kappa).
   if (p.f_scheme == PR_EXPLICIT_EULER) {
@@ -390,6 +397,16 @@ int parareal_set_option(pr_ctx* c, int option, double value) {
     case PR_OPT_CG_BLOCKS_PER_SM:
       if (!(value >= 0.0 && value <= 32.0)) return fail(c, PR_EINVAL, "blocks per SM must be in [0, 32]");
       c->opt_cg_bps = (int)value;
+      return PR_OK;
+    case PR_OPT_G_CHEBYSHEV:
+      if (!(value == 0.0 || (value >= 2.0 && value <= 64.0)))
+        return fail(c, PR_EINVAL, "Chebyshev steps must be 0 or in [2, 64]");
+      c->opt_g_cheb = (int)value;
+      if (c->opt_g_cheb && c->has_problem) {
+        cudaSetDevice(c->device);
+        PR_CUDA(c, cheb_alloc(c));
+        PR_CUDA(c, cudaStreamSynchronize(c->stream));
+      }
       return PR_OK;
     default:
       return fail(c, PR_EINVAL, "unknown option");

@@ -236,7 +236,7 @@ __device__ bool team_fine(const AsyncDev& a, const TeamBarrier& bar, const doubl
   return bar.sync();
 }
 
-__global__ void __launch_bounds__(ATHREADS) async_kernel(AsyncDev a) {
+__global__ void __launch_bounds__(ATHREADS, 2) async_kernel(AsyncDev a) {
   const int team = blockIdx.x / a.C;
   const int tb = blockIdx.x % a.C;
   const bool leader = tb == 0 && threadIdx.x == 0;

@@ -9,6 +9,10 @@
 // solution x is still in the workspace the kernel forms
 //     lam_i^{k+1} = (x + v_i) - w_i^k        (this operation order, no FMA)
 // its max-norm increment against lam_i^k (Eq. (22)), and stores w_i = x.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
 #include <cooperative_groups.h>
 
 #include "device.cuh"
@@ -20,6 +24,23 @@ namespace pr {
 namespace {
 
 constexpr int CG_THREADS = RED_THREADS;
+
+// Chebyshev-preconditioned CG (option PR_OPT_G_CHEBYSHEV): the preconditioner
+// z = p_m(B) r is m steps of Chebyshev iteration on the spectrum bounds [lo, hi]
+// of B = I + dT A, run in FP32 (the FP64 pipe is the scarce one on this GPU);
+// the CG recurrences, the residual and the stopping test stay FP64.
+constexpr int CHEB_MAX = 64;
+
+struct ChebDev {
+  int m;                      // 0: plain CG
+  double lo, hi;              // spectrum bounds of B
+  float inv_c;                // 1 / centre of [lo, hi]
+  float c1[CHEB_MAX], c2[CHEB_MAX];  // step k: d_k = c1[k] d_{k-1} + c2[k] res_k
+  float c0, rx, ry, rz;       // constant-kappa B in FP32 (off-diagonals -r)
+  StencilVar<float> gv32;     // variable-kappa B in FP32
+  double* z;                  // FP64 preconditioned residual
+  float *res, *y, *d0, *d1;   // FP32 Chebyshev vectors
+};
 
 struct CgDev {
   Geom g;
@@ -37,6 +58,7 @@ struct CgDev {
   CgWork ws;
   double rtol;
   int maxit;
+  ChebDev ch;
 };
 
 struct GridBarrier {
@@ -46,19 +68,233 @@ struct GridBarrier {
   }
 };
 
+// B d in FP32 at one point (coarse-operator form: diagonal c0, faces -c_f).
+__device__ __forceinline__ float op32(const Geom& g, const ChebDev& ch, bool var,
+                                      const float* __restrict__ u, int x, int y, int z,
+                                      long long idx) {
+  const long long plane = (long long)g.nx * g.ny;
+  const float w = x > 0 ? u[idx - 1] : 0.f;
+  const float e = x + 1 < g.nx ? u[idx + 1] : 0.f;
+  const float s = y > 0 ? u[idx - g.nx] : 0.f;
+  const float n = y + 1 < g.ny ? u[idx + g.nx] : 0.f;
+  const float bz = z > 0 ? u[idx - plane] : 0.f;
+  const float fz = z + 1 < g.nz ? u[idx + plane] : 0.f;
+  const float uc = u[idx];
+  if (!var) {
+    float res = ch.c0 * uc - ch.rx * (w + e);
+    if (g.dim > 1) res -= ch.ry * (s + n);
+    if (g.dim > 2) res -= ch.rz * (bz + fz);
+    return res;
+  }
+  const long long fx = ((long long)z * g.ny + y) * (g.nx + 1) + x;
+  float res = ch.gv32.c0[idx] * uc - ch.gv32.cx[fx] * w - ch.gv32.cx[fx + 1] * e;
+  if (g.dim > 1) {
+    const long long fy = ((long long)z * (g.ny + 1) + y) * g.nx + x;
+    res -= ch.gv32.cy[fy] * s + ch.gv32.cy[fy + g.nx] * n;
+  }
+  if (g.dim > 2) res -= ch.gv32.cz[idx] * bz + ch.gv32.cz[idx + plane] * fz;
+  return res;
+}
+
+#ifndef PR_CHEB_ROWS
+#define PR_CHEB_ROWS 2
+#endif
+constexpr int CHEB_U = PR_CHEB_ROWS;  // warp-rows in flight per trip of a Chebyshev step
+
+// One Chebyshev step on this block's rows: res -= B dp, dn = c1 dp + c2 res,
+// y += dn; with LAST also z = y (FP64) and the partial r.z.  CHEB_U warp-rows
+// per trip: the step is light FP32 work, so it is bound by load latency
+// unless several rows are in flight.
+template <bool LAST>
+__device__ __forceinline__ double cheb_step(const Geom& g, const ChebDev& ch, bool var,
+                                            const float* __restrict__ dp, float* __restrict__ dn,
+                                            float* __restrict__ res, float* __restrict__ y,
+                                            double* __restrict__ z, const double* __restrict__ r,
+                                            float c1, float c2, int blk, int nblk) {
+  const int lane = threadIdx.x & 31;
+  double acc = 0.0;
+  RowIter it[CHEB_U];
+#pragma unroll
+  for (int u = 0; u < CHEB_U; ++u) {
+    it[u] = RowIter(g, blk, nblk);
+    for (int v = 0; v < u; ++v) it[u].advance();
+  }
+  while (it[0].z < g.nz) {
+    long long idx[CHEB_U];
+    bool ok[CHEB_U];
+    float rs[CHEB_U], dv[CHEB_U], yv[CHEB_U];
+#pragma unroll
+    for (int u = 0; u < CHEB_U; ++u) {
+      const int x = it[u].seg * 32 + lane;
+      ok[u] = it[u].z < g.nz && x < g.nx;
+      idx[u] = ((long long)it[u].z * g.ny + it[u].y) * g.nx + x;
+      rs[u] = 0.f;
+      dv[u] = 0.f;
+      yv[u] = 0.f;
+      if (ok[u]) {
+        rs[u] = res[idx[u]] - op32(g, ch, var, dp, x, it[u].y, it[u].z, idx[u]);
+        dv[u] = c1 * dp[idx[u]] + c2 * rs[u];
+        yv[u] = y[idx[u]] + dv[u];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < CHEB_U; ++u) {
+      if (ok[u]) {
+        res[idx[u]] = rs[u];
+        dn[idx[u]] = dv[u];
+        y[idx[u]] = yv[u];
+        if (LAST) {
+          const double zi = static_cast<double>(yv[u]);
+          z[idx[u]] = zi;
+          acc = fma(r[idx[u]], zi, acc);
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < CHEB_U; ++v) it[u].advance();
+    }
+  }
+  return acc;
+}
+
+// Preconditioned CG (Hestenes-Stiefel with z = p_m(B) r), same start, stopping
+// rule and return value as cg_core.  Per iteration: q = B p and p.q (reduction);
+// x, r and r.r, which also starts the preconditioner res = r, d_0 = res / c,
+// y = d_0 (reduction); m - 1 Chebyshev steps
+//   res -= B d_{k-1},  d_k = rho_k rho_{k-1} d_{k-1} + (2 rho_k / e) res,  y += d_k
+// (one grid barrier each; the last one writes z = y and reduces r.z); then
+// p = z + beta p.
+__device__ int pcg_core(const CgDev& a, int nblk, int blk) {
+  const Geom& g = a.g;
+  const ChebDev& ch = a.ch;
+  const CgWork& ws = a.ws;
+  const bool var = a.var != 0;
+  const long long M = g.M;
+  const long long t0 = blk * (long long)blockDim.x + threadIdx.x;
+  const long long nt = (long long)nblk * blockDim.x;
+  const GridBarrier bar{};
+  int parity = 0;
+  auto part = [&]() { return ws.part + (size_t)parity * 3 * nblk; };
+  double s_rr = 0.0, s_bb = 0.0;
+  for_each_point(g, blk, nblk, [&](int x, int y, int z, long long i) {
+    const double bi = a.b[i];
+    const double ri = bi - gop_xyz(g, a.k, var, a.gv, a.x0, x, y, z, i);
+    ws.x[i] = a.x0[i];
+    ws.r[i] = ri;
+    const float rf = static_cast<float>(ri);
+    const float d = rf * ch.inv_c;
+    ch.res[i] = rf;
+    ch.d0[i] = d;
+    ch.y[i] = d;
+    s_rr += ri * ri;
+    s_bb += bi * bi;
+  });
+  {
+    const double v[2] = {s_rr, s_bb};
+    block_sum<2>(v, part(), blk);
+  }
+  bar.sync();
+  const int maxit = a.maxit;
+  const double rtol = a.rtol;
+  const StencilConst& k = a.k;
+  double o8[8];
+  group_sum<2, 8>(part(), nblk, o8, [&](double* r) {
+    r[2] = rtol * sqrt(r[1]);
+    r[3] = (sqrt(r[0]) <= r[2] || r[0] == 0.0 || maxit <= 0) ? 1.0 : 0.0;
+    r[4] = k.c0 / k.rx;
+    r[5] = k.ry / k.rx;
+    r[6] = k.rz / k.rx;
+    r[7] = 1.0 / k.rx;
+  });
+  parity ^= 1;
+  const double thresh = o8[2];
+  if (o8[3] != 0.0) return 0;
+  const bool scaled = !var;
+  const StencilConst ks = scaled ? StencilConst{o8[4], 1.0, o8[5], o8[6]} : k;
+  const double sc = scaled ? o8[7] : 1.0;
+  int it = 0;
+  double rz = 0.0, beta = 0.0;
+  while (true) {
+    // ---- z = p_m(B) r: steps k = 1..m-1 (res, d_0, y set by the previous pass)
+    for (int kk = 1; kk < ch.m; ++kk) {
+      const float c1 = ch.c1[kk], c2 = ch.c2[kk];
+      const float* dp = (kk & 1) ? ch.d0 : ch.d1;
+      float* dn = (kk & 1) ? ch.d1 : ch.d0;
+      const bool last = kk == ch.m - 1;
+      double s_rz = 0.0;
+      if (last)
+        s_rz = cheb_step<true>(g, ch, var, dp, dn, ch.res, ch.y, ch.z, ws.r, c1, c2, blk, nblk);
+      else
+        cheb_step<false>(g, ch, var, dp, dn, ch.res, ch.y, ch.z, ws.r, c1, c2, blk, nblk);
+      if (last) {
+        const double v[1] = {s_rz};
+        block_sum<1>(v, part(), blk);
+      }
+      bar.sync();
+      if (last) {
+        double o2[2];
+        group_sum<1, 2>(part(), nblk, o2, [&](double* r) { r[1] = it == 0 ? 0.0 : r[0] / rz; });
+        parity ^= 1;
+        beta = o2[1];
+        rz = o2[0];
+      }
+    }
+    // ---- p = z + beta p (p = z on the first iteration)
+    for (long long i = t0; i < M; i += nt) ws.p[i] = it == 0 ? ch.z[i] : fma(beta, ws.p[i], ch.z[i]);
+    bar.sync();
+    // ---- q = B p, p.q
+    {
+      const double v[1] = {cg_matvec_dot(g, ks, var, scaled, a.gv, ws.p, ws.q, blk, nblk)};
+      block_sum<1>(v, part(), blk);
+    }
+    bar.sync();
+    double o2[2];
+    group_sum<1, 2>(part(), nblk, o2, [&](double* r) { r[1] = rz / r[0]; });
+    parity ^= 1;
+    const double alpha = o2[1];
+    // ---- x, r, r.r; start the next preconditioner application
+    double s0 = 0.0;
+    for (long long i = t0; i < M; i += nt) {
+      const double ri = fma(-alpha, ws.q[i], ws.r[i]);
+      ws.x[i] = fma(alpha * sc, ws.p[i], ws.x[i]);
+      ws.r[i] = ri;
+      s0 = fma(ri, ri, s0);
+      const float rf = static_cast<float>(ri);
+      const float d = rf * ch.inv_c;
+      ch.res[i] = rf;
+      ch.d0[i] = d;
+      ch.y[i] = d;
+    }
+    {
+      const double v[1] = {s0};
+      block_sum<1>(v, part(), blk);
+    }
+    bar.sync();
+    ++it;
+    group_sum<1, 2>(part(), nblk, o2, [&](double* r) {
+      r[1] = (sqrt(r[0]) <= thresh || r[0] == 0.0 || it >= maxit) ? 1.0 : 0.0;
+    });
+    parity ^= 1;
+    if (o2[1] != 0.0) return it;
+  }
+}
+
 // MINB = blocks per SM the register budget must allow.  The CG vectors of a
 // grid up to about 2 M points stay in L2 and 2 blocks/SM are best (fewer
 // partials and barrier arrivals); beyond that the phases stream from HBM and
 // are latency-bound, so a 4-blocks/SM instance (<= 64 registers) keeps twice
 // as many loads in flight (measured 707 -> ~550 us per iteration at 256^3).
-template <int MINB>
+template <int MINB, bool PCG>
 __global__ void __launch_bounds__(CG_THREADS, MINB) cg_kernel(CgDev a) {
   const long long M = a.g.M;
   const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long nt = (long long)gridDim.x * blockDim.x;
   if (a.mode == CG_CORRECT && t0 == 0) *a.delta = 0ull;
-  const int it = cg_core(a.g, a.k, a.var != 0, a.gv, a.b, a.x0, a.rtol, a.maxit, a.ws,
-                         GridBarrier{}, gridDim.x, blockIdx.x);
+  int it;
+  if constexpr (PCG)
+    it = pcg_core(a, gridDim.x, blockIdx.x);
+  else
+    it = cg_core(a.g, a.k, a.var != 0, a.gv, a.b, a.x0, a.rtol, a.maxit, a.ws, GridBarrier{},
+                 gridDim.x, blockIdx.x);
   // epilogue (x is final in the workspace)
   const double* x = a.ws.x;
   if (a.mode == CG_PLAIN) {
@@ -109,10 +345,10 @@ __global__ void copy_kernel(double* __restrict__ d, const double* __restrict__ s
 
 constexpr long long CG_L2_POINTS = 2LL << 20;  // 5 FP64 vectors of 2 M points = 80 MB
 
-template <int MINB>
+template <int MINB, bool PCG = false>
 int cg_blocks_of(int num_sms) {
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_kernel<MINB>, CG_THREADS, 0) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_kernel<MINB, PCG>, CG_THREADS, 0) !=
           cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
@@ -123,7 +359,8 @@ int cg_blocks_of(int num_sms) {
 }  // namespace
 
 int cg_max_blocks(int num_sms) {
-  const int a = cg_blocks_of<2>(num_sms), b = cg_blocks_of<4>(num_sms);
+  const int a = std::max(cg_blocks_of<2>(num_sms), cg_blocks_of<4>(num_sms));
+  const int b = std::max(cg_blocks_of<2, true>(num_sms), cg_blocks_of<4, true>(num_sms));
   return a > b ? a : b;
 }
 
@@ -144,8 +381,37 @@ cudaError_t cg_solve(pr_ctx* c, const CgArgs& in) {
   a.ws = {c->cg_x, c->cg_r, c->cg_p, c->cg_q, c->cg_part};
   a.rtol = c->prob.g_rtol;
   a.maxit = c->prob.g_maxit;
+  if (c->opt_g_cheb >= 2 && c->cheb_z) {
+    ChebDev& ch = a.ch;
+    ch.m = c->opt_g_cheb;
+    ch.lo = c->g_lo;
+    ch.hi = c->g_hi;
+    // Chebyshev recurrence coefficients on [lo, hi] (centre cc, half width ee)
+    const double cc = 0.5 * (c->g_hi + c->g_lo), ee = 0.5 * (c->g_hi - c->g_lo);
+    const double sigma = cc / ee;
+    double rho = 1.0 / sigma;
+    ch.inv_c = static_cast<float>(1.0 / cc);
+    for (int k = 1; k < ch.m; ++k) {
+      const double rho_n = 1.0 / (2.0 * sigma - rho);
+      ch.c1[k] = static_cast<float>(rho_n * rho);
+      ch.c2[k] = static_cast<float>(2.0 * rho_n / ee);
+      rho = rho_n;
+    }
+    ch.c0 = static_cast<float>(c->gst.c0);
+    ch.rx = static_cast<float>(c->gst.rx);
+    ch.ry = static_cast<float>(c->gst.ry);
+    ch.rz = static_cast<float>(c->gst.rz);
+    ch.gv32 = c->gvar32;
+    ch.z = c->cheb_z;
+    ch.res = c->cheb_f32;
+    ch.y = ch.res + c->g.M;
+    ch.d0 = ch.y + c->g.M;
+    ch.d1 = ch.d0 + c->g.M;
+  }
   const bool big = c->g.M > CG_L2_POINTS;
-  int cap = big ? cg_blocks_of<4>(c->num_sms) : cg_blocks_of<2>(c->num_sms);
+  const bool pcg = a.ch.m >= 2;
+  int cap = big ? (pcg ? cg_blocks_of<4, true>(c->num_sms) : cg_blocks_of<4>(c->num_sms))
+                : (pcg ? cg_blocks_of<2, true>(c->num_sms) : cg_blocks_of<2>(c->num_sms));
   // a caller-chosen blocks-per-SM cap leaves room for concurrent kernels
   if (c->opt_cg_bps > 0 && c->opt_cg_bps * c->num_sms < cap) cap = c->opt_cg_bps * c->num_sms;
   long long want = (c->g.M + CG_THREADS * 4 - 1) / (CG_THREADS * 4);
@@ -153,8 +419,127 @@ cudaError_t cg_solve(pr_ctx* c, const CgArgs& in) {
   if (blocks > c->cg_blocks) blocks = c->cg_blocks;  // partials are sized for cg_blocks
   if (blocks < 1) blocks = 1;
   void* args[] = {&a};
-  return cudaLaunchCooperativeKernel(big ? (void*)cg_kernel<4> : (void*)cg_kernel<2>, dim3(blocks),
-                                     dim3(CG_THREADS), args, 0, c->stream);
+  void* fn = big ? (pcg ? (void*)cg_kernel<4, true> : (void*)cg_kernel<4, false>)
+                 : (pcg ? (void*)cg_kernel<2, true> : (void*)cg_kernel<2, false>);
+  return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(CG_THREADS), args, 0, c->stream);
+}
+
+namespace {
+
+__device__ __forceinline__ void atomic_max_pos(unsigned long long* a, double v) {
+  atomicMax(a, (unsigned long long)__double_as_longlong(v));
+}
+__device__ __forceinline__ void atomic_min_pos(unsigned long long* a, double v) {
+  atomicMin(a, (unsigned long long)__double_as_longlong(v));
+}
+
+// out[0] = min face kappa, out[1] = max face kappa, out[2] = max diagonal of
+// I + dT A (bits of positive doubles, which order like the values); the face
+// arrays hold dT kappa_f / h^2.
+__global__ void bounds_kernel(Geom g, StencilVar<double> gv, double dT,
+                              unsigned long long* out) {
+  const long long nfx = (long long)(g.nx + 1) * g.ny * g.nz;
+  const long long nfy = g.dim > 1 ? (long long)g.nx * (g.ny + 1) * g.nz : 0;
+  const long long nfz = g.dim > 2 ? (long long)g.nx * g.ny * (g.nz + 1) : 0;
+  double kmin = 1e300, kmax = 0.0, dmax = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nfx + nfy + nfz + g.M;
+       t += (long long)gridDim.x * blockDim.x) {
+    double kf = -1.0;
+    if (t < nfx) kf = gv.cx[t] * g.hx * g.hx / dT;
+    else if (t < nfx + nfy) kf = gv.cy[t - nfx] * g.hy * g.hy / dT;
+    else if (t < nfx + nfy + nfz) kf = gv.cz[t - nfx - nfy] * g.hz * g.hz / dT;
+    else dmax = fmax(dmax, gv.c0[t - nfx - nfy - nfz]);
+    if (kf >= 0.0) {
+      kmin = fmin(kmin, kf);
+      kmax = fmax(kmax, kf);
+    }
+  }
+  atomic_min_pos(out, kmin);
+  atomic_max_pos(out + 1, kmax);
+  atomic_max_pos(out + 2, dmax);
+}
+
+__global__ void to_f32_kernel(const double* __restrict__ a, float* __restrict__ b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    b[i] = static_cast<float>(a[i]);
+}
+
+}  // namespace
+
+// Spectrum bounds [lo, hi] of I + dT A (the Chebyshev preconditioner's
+// interval): exact for constant kappa (extreme discrete sine modes); for
+// variable kappa lo = 1 + dT kmin lambda_min(A_1) and hi = min(Gershgorin,
+// 1 + dT kmax lambda_max(A_1)) with kmin/kmax over the faces.
+cudaError_t coarse_bounds(pr_ctx* c) {
+  const Geom& g = c->g;
+  const int n[3] = {g.nx, g.ny, g.nz};
+  const double h[3] = {g.hx, g.hy, g.hz};
+  double lo1 = 0.0, hi1 = 0.0;
+  for (int ax = 0; ax < g.dim; ++ax) {
+    const double s1 = sin(M_PI * h[ax] / 2.0), sn = sin(n[ax] * M_PI * h[ax] / 2.0);
+    lo1 += 4.0 / (h[ax] * h[ax]) * s1 * s1;
+    hi1 += 4.0 / (h[ax] * h[ax]) * sn * sn;
+  }
+  const double dT = c->dT;
+  if (!c->var_kappa) {
+    c->g_lo = 1.0 + dT * lo1;
+    c->g_hi = 1.0 + dT * hi1;
+    return cudaSuccess;
+  }
+  const double big = 1e300;
+  unsigned long long init[3] = {0ull, 0ull, 0ull};
+  memcpy(&init[0], &big, sizeof big);
+  unsigned long long* d = reinterpret_cast<unsigned long long*>(c->cg_part);  // scratch
+  cudaError_t e = cudaMemcpyAsync(d, init, sizeof init, cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return e;
+  bounds_kernel<<<c->num_sms * 4, 256, 0, c->stream>>>(g, c->gvar, dT, d);
+  unsigned long long res[3];
+  e = cudaMemcpyAsync(res, d, sizeof res, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return e;
+  double v[3];
+  memcpy(v, res, sizeof v);
+  const double gersh = 2.0 * v[2] - 1.0;  // 1 + 2 * (diag - 1)
+  c->g_lo = 1.0 + dT * v[0] * lo1;
+  c->g_hi = std::min(gersh, 1.0 + dT * v[1] * hi1);
+  return cudaSuccess;
+}
+
+// Workspaces of the Chebyshev-preconditioned coarse CG (z, four FP32 vectors,
+// FP32 copies of the variable-kappa arrays); allocated when the option is on.
+cudaError_t cheb_alloc(pr_ctx* c) {
+  if (c->cheb_z) return cudaSuccess;
+  const Geom& g = c->g;
+  cudaError_t e = cudaMalloc(&c->cheb_z, g.M * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&c->cheb_f32, 4 * g.M * sizeof(float));
+  if (e == cudaSuccess && c->var_kappa) {
+    const long long nfx = (long long)(g.nx + 1) * g.ny * g.nz;
+    const long long nfy = g.dim > 1 ? (long long)g.nx * (g.ny + 1) * g.nz : 0;
+    const long long nfz = g.dim > 2 ? (long long)g.nx * g.ny * (g.nz + 1) : 0;
+    const long long total = g.M + nfx + nfy + nfz;
+    e = cudaMalloc(&c->gcoef32, total * sizeof(float));
+    if (e == cudaSuccess) {
+      to_f32_kernel<<<c->num_sms * 8, 256, 0, c->stream>>>(c->gcoef, c->gcoef32, total);
+      e = cudaGetLastError();
+      float* q0 = c->gcoef32;
+      float* qx = q0 + g.M;
+      float* qy = qx + nfx;
+      float* qz = qy + nfy;
+      c->gvar32 = {q0, qx, nfy ? qy : nullptr, nfz ? qz : nullptr};
+    }
+  }
+  return e;
+}
+
+void cheb_free(pr_ctx* c) {
+  if (c->cheb_z) cudaFree(c->cheb_z);
+  if (c->cheb_f32) cudaFree(c->cheb_f32);
+  if (c->gcoef32) cudaFree(c->gcoef32);
+  c->cheb_z = nullptr;
+  c->cheb_f32 = nullptr;
+  c->gcoef32 = nullptr;
+  c->gvar32 = {};
 }
 
 cudaError_t correct(pr_ctx* c, const double* w_new, const double* v, const double* w_old,

@@ -71,9 +71,10 @@ struct pr_ctx {
   double* fcoef = nullptr;   // F: c0, cx, cy, cz (FP64)
   float* fcoef32 = nullptr;  // F: FP32 copy for the mixed form
   double* gcoef = nullptr;   // G: c0, cx, cy, cz
+  float* gcoef32 = nullptr;  // G in FP32 (Chebyshev preconditioner, variable kappa)
   double* fsys0 = nullptr;   // trapezoidal F, variable kappa: diagonal of I + dt/2 A
   pr::StencilVar<double> fvar{}, gvar{}, fsysvar{};
-  pr::StencilVar<float> fvar32{};
+  pr::StencilVar<float> fvar32{}, gvar32{};
   // 1D implicit tables
   pr::TriTables tri_f{}, tri_g{};
   // workspaces
@@ -101,6 +102,10 @@ struct pr_ctx {
   int opt_pipeline = 0;      // overlap F of iteration k+1 with the coarse sweep of k
   int opt_chunks = 8;        // slice chunks per pipelined fine batch
   int opt_cg_bps = 0;        // CG blocks per SM (0 = automatic)
+  int opt_g_cheb = 0;        // Chebyshev steps of the coarse CG preconditioner (0 = plain CG)
+  double g_lo = 0, g_hi = 0; // spectrum bounds of I + dT A
+  double* cheb_z = nullptr;  // preconditioned residual (M)
+  float* cheb_f32 = nullptr; // FP32 Chebyshev vectors (4 M)
   // pipelined driver resources (created lazily)
   cudaStream_t s_sweep = nullptr, s_fine = nullptr;
   double* v2 = nullptr;      // second fine-output buffer (N*M)
@@ -176,6 +181,9 @@ struct CgArgs {
   int mode;
 };
 cudaError_t cg_solve(pr_ctx* c, const CgArgs& a);
+cudaError_t coarse_bounds(pr_ctx* c);
+cudaError_t cheb_alloc(pr_ctx* c);
+void cheb_free(pr_ctx* c);
 int cg_max_blocks(int num_sms);
 cudaError_t correct(pr_ctx* c, const double* w_new, const double* v, const double* w_old,
                     double* lam, unsigned long long* delta);

@@ -9,25 +9,57 @@
 namespace pr {
 
 // ----------------------------------------------------------------- stencils
+// Warp-row iterator of a group of `nblk` blocks (this one is `blk`): warp w of
+// the group visits items w, w + nw, w + 2 nw, ... of the (z, y, x-segment)
+// enumeration, each item 32 consecutive x of one row.  The start and the
+// stride are split into (segment, y, z) once; each step then advances with
+// carries instead of 64-bit divisions (an emulated multi-instruction sequence
+// per division, which dominates the integer work of a light pass).
+struct RowIter {
+  int seg, y, z;     // current item
+  int dseg, dy, dz;  // the stride nw split the same way
+  int xseg, ny;
+  RowIter() = default;
+  __device__ __forceinline__ RowIter(const Geom& g, int blk, int nblk) {
+    const int wpb = blockDim.x >> 5;
+    const long long gw = (long long)blk * wpb + (threadIdx.x >> 5);
+    const long long nw = (long long)nblk * wpb;
+    xseg = (g.nx + 31) >> 5;
+    ny = g.ny;
+    const long long row = gw / xseg, drow = nw / xseg;
+    seg = (int)(gw - row * xseg);
+    y = (int)(row % g.ny);
+    z = (int)(row / g.ny);
+    dseg = (int)(nw - drow * xseg);
+    dy = (int)(drow % g.ny);
+    dz = (int)(drow / g.ny);
+  }
+  __device__ __forceinline__ void advance() {
+    seg += dseg;
+    y += dy;
+    z += dz;
+    if (seg >= xseg) {
+      seg -= xseg;
+      ++y;
+    }
+    if (y >= ny) {
+      y -= ny;
+      ++z;
+    }
+  }
+};
+
 // Visit every grid point with a group of `nblk` blocks (this one is `blk`):
 // each warp takes 32 consecutive x of one (y, z) row, so the row's coordinates
-// are derived once per 32 points instead of by a 64-bit division per point.
+// are derived once per 32 points (RowIter).
 // f(x, y, z, idx) is called for every interior point exactly once.
 template <class Fn>
 __device__ __forceinline__ void for_each_point(const Geom& g, int blk, int nblk, Fn&& f) {
   const int lane = threadIdx.x & 31;
-  const int wpb = blockDim.x >> 5;
-  const long long gw = (long long)blk * wpb + (threadIdx.x >> 5);
-  const long long nw = (long long)nblk * wpb;
-  const int xseg = (g.nx + 31) >> 5;
-  const long long items = (long long)g.ny * g.nz * xseg;
-  for (long long it = gw; it < items; it += nw) {
-    const long long row = it / xseg;
-    const int x = (int)(it - row * xseg) * 32 + lane;
+  for (RowIter r(g, blk, nblk); r.z < g.nz; r.advance()) {
+    const int x = r.seg * 32 + lane;
     if (x >= g.nx) continue;
-    const int y = (int)(row % g.ny);
-    const int z = (int)(row / g.ny);
-    f(x, y, z, row * g.nx + x);
+    f(x, r.y, r.z, ((long long)r.z * g.ny + r.y) * g.nx + x);
   }
 }
 
@@ -124,9 +156,13 @@ __device__ __forceinline__ void block_sum(const double (&v)[NV], double* part, i
 }
 
 // Sum of nblk block partials in a fixed order; identical result in every block.
-template <int NV>
-__device__ __forceinline__ void group_sum(const double* part, int nblk, double (&o)[NV]) {
-  __shared__ double res[3];
+// `derive` runs in thread 0 on the sums (slots 0..NV-1) and may fill slots
+// NV..7 with scalars computed from them: a division or square root then costs
+// one thread per block instead of every thread (FP64 division and square root
+// are multi-instruction sequences on the FP64 pipe, the scarce one here).
+template <int NV, int NO, class Fn>
+__device__ __forceinline__ void group_sum(const double* part, int nblk, double (&o)[NO], Fn&& derive) {
+  __shared__ double res[8];
   if (threadIdx.x < 32) {
 #pragma unroll
     for (int j = 0; j < NV; ++j) {
@@ -135,11 +171,17 @@ __device__ __forceinline__ void group_sum(const double* part, int nblk, double (
       s = warp_sum(s);
       if (threadIdx.x == 0) res[j] = s;
     }
+    if (threadIdx.x == 0) derive(res);
   }
   __syncthreads();
 #pragma unroll
-  for (int j = 0; j < NV; ++j) o[j] = res[j];
+  for (int j = 0; j < NO; ++j) o[j] = res[j];
   __syncthreads();
+}
+
+template <int NV>
+__device__ __forceinline__ void group_sum(const double* part, int nblk, double (&o)[NV]) {
+  group_sum<NV, NV>(part, nblk, o, [](double*) {});
 }
 
 __device__ __forceinline__ unsigned long long abs_bits(double d) {
@@ -284,23 +326,20 @@ __device__ __forceinline__ double cg_matvec_dot(const Geom& g, const StencilCons
                                                 const double* __restrict__ p,
                                                 double* __restrict__ q, int blk, int nblk) {
   const int lane = threadIdx.x & 31;
-  const int wpb = blockDim.x >> 5;
-  const long long gw = (long long)blk * wpb + (threadIdx.x >> 5);
-  const long long nw = (long long)nblk * wpb;
-  const int xseg = (g.nx + 31) >> 5;
-  const long long items = (long long)g.ny * g.nz * xseg;
   double sa = 0.0, sb = 0.0;
-  for (long long it = gw; it < items; it += 2 * nw) {
-    const long long itb = it + nw;
-    const long long ra = it / xseg, rb = itb / xseg;
-    const int xa = (int)(it - ra * xseg) * 32 + lane;
-    const int xb = (int)(itb - rb * xseg) * 32 + lane;
+  // items j and j + 1 of this warp's sequence on each trip
+  RowIter ra(g, blk, nblk), rb(g, blk, nblk);
+  rb.advance();
+  while (ra.z < g.nz) {
+    const int xa = ra.seg * 32 + lane;
+    const int xb = rb.seg * 32 + lane;
     const bool oka = xa < g.nx;
-    const bool okb = itb < items && xb < g.nx;
-    const long long ia = ra * g.nx + xa, ib = rb * g.nx + xb;
+    const bool okb = rb.z < g.nz && xb < g.nx;
+    const long long ia = ((long long)ra.z * g.ny + ra.y) * g.nx + xa;
+    const long long ib = ((long long)rb.z * g.ny + rb.y) * g.nx + xb;
     double qa = 0.0, qb = 0.0;
-    if (oka) qa = op_point(g, k, var, scaled, gv, p, xa, (int)(ra % g.ny), (int)(ra / g.ny), ia);
-    if (okb) qb = op_point(g, k, var, scaled, gv, p, xb, (int)(rb % g.ny), (int)(rb / g.ny), ib);
+    if (oka) qa = op_point(g, k, var, scaled, gv, p, xa, ra.y, ra.z, ia);
+    if (okb) qb = op_point(g, k, var, scaled, gv, p, xb, rb.y, rb.z, ib);
     if (oka) {
       q[ia] = qa;
       sa = fma(p[ia], qa, sa);
@@ -309,6 +348,10 @@ __device__ __forceinline__ double cg_matvec_dot(const Geom& g, const StencilCons
       q[ib] = qb;
       sb = fma(p[ib], qb, sb);
     }
+    ra.advance();
+    ra.advance();
+    rb.advance();
+    rb.advance();
   }
   return sa + sb;
 }
@@ -379,20 +422,27 @@ __device__ int cg_core(const Geom& g, const StencilConst& k, bool var, const Ste
     block_sum<2>(v, part(), blk);
   }
   if (!bar.sync()) return -1;
-  double o2[2];
-  group_sum<2>(part(), nblk, o2);
+  // scalars derived once per block by thread 0: threshold, stop flag and the
+  // coefficients of the operator scaled by 1/R_x (constant kappa): q' = q / R_x,
+  // alpha' = rr / p.q' = R_x alpha; r -= alpha' q', x += (alpha' / R_x) p
+  double o8[8];
+  group_sum<2, 8>(part(), nblk, o8, [&](double* r) {
+    r[2] = rtol * sqrt(r[1]);
+    r[3] = (sqrt(r[0]) <= r[2] || r[0] == 0.0 || maxit <= 0) ? 1.0 : 0.0;
+    r[4] = k.c0 / k.rx;
+    r[5] = k.ry / k.rx;
+    r[6] = k.rz / k.rx;
+    r[7] = 1.0 / k.rx;
+  });
   parity ^= 1;
-  double rr = o2[0];
-  const double bb = o2[1];
-  const double thresh = rtol * sqrt(bb);
+  double rr = o8[0];
+  const double thresh = o8[2];
   int it = 0;
-  bool done = sqrt(rr) <= thresh || rr == 0.0 || maxit <= 0;
+  bool done = o8[3] != 0.0;
 #if PR_CG_FAST
-  // the passes take the operator scaled by 1/R_x (constant kappa): q' = q / R_x,
-  // so alpha' = rr / p.q' = R_x alpha; r -= alpha' q', x += (alpha' / R_x) p
   const bool scaled = !var;
-  const StencilConst ks = scaled ? StencilConst{k.c0 / k.rx, 1.0, k.ry / k.rx, k.rz / k.rx} : k;
-  const double sc = scaled ? 1.0 / k.rx : 1.0;
+  const StencilConst ks = scaled ? StencilConst{o8[4], 1.0, o8[5], o8[6]} : k;
+  const double sc = scaled ? o8[7] : 1.0;
 #endif
   while (!done) {
 #if PR_CG_FAST
@@ -416,10 +466,10 @@ __device__ int cg_core(const Geom& g, const StencilConst& k, bool var, const Ste
     }
 #endif
     if (!bar.sync()) return -1;
-    double o1[1];
-    group_sum<1>(part(), nblk, o1);
+    double o2[2];
+    group_sum<1, 2>(part(), nblk, o2, [&](double* r) { r[1] = rr / r[0]; });
     parity ^= 1;
-    const double alpha = rr / o1[0];
+    const double alpha = o2[1];
 #if PR_CG_FAST
     {
       const double v[1] = {cg_update_xr(ws.x, ws.r, ws.p, ws.q, alpha * sc, alpha, t0, nt, M)};
@@ -451,13 +501,17 @@ __device__ int cg_core(const Geom& g, const StencilConst& k, bool var, const Ste
     }
 #endif
     if (!bar.sync()) return -1;
-    group_sum<1>(part(), nblk, o1);
-    parity ^= 1;
-    const double rr_new = o1[0];
     ++it;
-    done = sqrt(rr_new) <= thresh || rr_new == 0.0 || it >= maxit;
+    double o3[3];
+    group_sum<1, 3>(part(), nblk, o3, [&](double* r) {
+      r[1] = (sqrt(r[0]) <= thresh || r[0] == 0.0 || it >= maxit) ? 1.0 : 0.0;
+      r[2] = r[0] / rr;
+    });
+    parity ^= 1;
+    const double rr_new = o3[0];
+    done = o3[1] != 0.0;
     if (!done) {
-      const double beta = rr_new / rr;
+      const double beta = o3[2];
 #if PR_CG_FAST
       cg_update_p(ws.p, ws.r, beta, t0, nt, M);
 #else
