@@ -103,6 +103,30 @@ def test_fine_fp32_vectorized_3d(n, var):
         assert 1e-12 < err < MIXED_TOL, (s, err)
 
 
+@pytest.mark.parametrize("n,f_steps", [((37, 19, 70), 2), ((37, 19, 70), 7), ((64, 8, 33), 4),
+                                        ((5, 3, 2), 3), ((33, 9, 97), 6)])
+def test_fine_fp32_3d_ragged_chunks_and_step_counts(n, f_steps):
+    """FP32 3D constant-kappa F: ragged x/y tiles, several and ragged z chunks, nx % 4 != 0
+    (scalar kernel) and == 0 (vector kernel), even and odd step counts, two steps (the
+    first reads FP64, the last writes FP64)."""
+    rng = np.random.default_rng(16)
+    h = tuple(1.0 / (m + 1) for m in n)
+    shape = tuple(reversed(n))
+    p = dict(dim=3, n=n, h=h, N=3, f_steps=f_steps, dt=0.15 * min(h) ** 2, f_scheme="explicit",
+             g_solver="cg", g_rtol=1e-10, f_prec=32, kappa=None, u0=rng.standard_normal(shape),
+             tol=0.0)
+    P = oracle_props(p)
+    X = rng.standard_normal((3,) + shape)
+    with Ctx(p) as c:
+        xin = dev(X)
+        out = torch().empty_like(xin)
+        pr.parareal_fine(c.ctx, xin, out, 3)
+        got = host(out).reshape(X.shape)
+    for s in range(3):
+        err = rel_l2(got[s], P.F(X[s]))
+        assert 1e-12 < err < MIXED_TOL, (s, err)
+
+
 @pytest.mark.parametrize("case", list(CASES))
 def test_coarse_propagator(case):
     p = CASES[case]()
