@@ -58,8 +58,8 @@ WORKLOADS = {
 # Constant kappa, explicit: the library runs the scaled form (states carried as
 # u / rx^j, which removes the x multiplier): 1D 1 DADD + 1 DFMA, 2D 2 DADD + 2 DFMA,
 # 3D 3 DADD + 3 DFMA, plus one DMUL on the steps that return to u (every R steps and
-# the last one, R = floor(100 / log10(1/rx))).  The asynchronous kernel's fine steps
-# use the plain form (scaled=False): 1 DMUL + d DADD + d DFMA.  Variable kappa:
+# the last one, R = floor(100 / log10(1/rx))), in the batched and the asynchronous
+# kernels alike.  Plain form (scaled=False): 1 DMUL + d DADD + d DFMA.  Variable kappa:
 # 1 DMUL + 2d DFMA.  1D implicit step by the partition solver: 2 (forward) + 1 (back)
 # + 2 (rebuild).
 def fp64_ops_per_lup(p, scaled=True):
@@ -383,7 +383,7 @@ def run_async_workload(args, local):
         f_ops = (CN_OPS_PER_CG_POINT[p["dim"]] * st.fine_cg_iterations * M
                  + CN_OPS_PER_LUP[p["dim"]] * st.fine_lups)
     elif p.get("f_prec", 64) == 64:
-        f_ops = st.fine_lups * fp64_ops_per_lup(p, scaled=False)
+        f_ops = st.fine_lups * fp64_ops_per_lup(p)
     else:
         f_ops = 0
     fp64_ops = st.cg_iterations * M * cg_ops + f_ops

@@ -31,6 +31,8 @@
 #include <algorithm>
 #include <vector>
 
+#include <cmath>
+
 #include "device.cuh"
 
 namespace pr {
@@ -60,6 +62,12 @@ struct AsyncDev {
   double f_rtol;
   int f_maxit;
   int tcg_stride;                 // vectors per team in tcg (4, or 5 with the trapezoidal rhs)
+  // scaled FP64 explicit steps (constant kappa): coefficients {c0/rx, -, ry/rx, rz/rx},
+  // return period R (0: plain form) and the factors rx^R and rx^(steps since the
+  // last return, at the final step)
+  StencilConst fsc;
+  int f_period;
+  double f_sigma_R, f_sigma_last;
   unsigned long long* fine_cg;    // CG iterations of the trapezoidal fine steps
   const double* u0;
   // per slice (index i-1)
@@ -194,6 +202,46 @@ __device__ bool team_fine_cn(const AsyncDev& a, const TeamBarrier& bar, const do
   return true;
 }
 
+// FP64 constant-kappa fine propagation in the scaled form (as the batched
+// kernel): the team carries v = u / sigma with sigma multiplied by rx every
+// step, v' = (c0/rx) v + (w + e) + (ry/rx)(s + n) + (rz/rx)(b + f), and returns
+// to u (times sigma = rx^j) every R steps and on the last step.
+__device__ bool team_fine_scaled(const AsyncDev& a, const TeamBarrier& bar, const double* xs,
+                                 double* v, double* pp0, double* pp1, int tb) {
+  const Geom& g = a.g;
+  const double ca = a.fsc.c0, cb = a.fsc.ry, cc = a.fsc.rz;
+  const int S = a.f_steps, R = a.f_period;
+  const double* src = xs;
+  int since = 0;
+  for (int s = 0; s < S; ++s) {
+    double* dst = (s == S - 1) ? v : ((s & 1) ? pp1 : pp0);
+    ++since;
+    const bool back = s == S - 1 || since == R;
+    const double sig = s == S - 1 ? a.f_sigma_last : a.f_sigma_R;
+    const long long plane = (long long)g.nx * g.ny;
+    for_each_point(g, tb, a.C, [&](int x, int y, int z, long long i) {
+      const double w = x > 0 ? src[i - 1] : 0.0;
+      const double e = x + 1 < g.nx ? src[i + 1] : 0.0;
+      double res = fma(ca, src[i], w + e);
+      if (g.dim > 1) {
+        const double sv = y > 0 ? src[i - g.nx] : 0.0;
+        const double nv = y + 1 < g.ny ? src[i + g.nx] : 0.0;
+        res = fma(cb, sv + nv, res);
+      }
+      if (g.dim > 2) {
+        const double bv = z > 0 ? src[i - plane] : 0.0;
+        const double fv = z + 1 < g.nz ? src[i + plane] : 0.0;
+        res = fma(cc, bv + fv, res);
+      }
+      dst[i] = back ? res * sig : res;
+    });
+    if (back) since = 0;
+    if (!bar.sync()) return false;
+    src = dst;
+  }
+  return true;
+}
+
 // Fine propagation v = F(xs_i) by the team: f_steps explicit steps, one team
 // barrier after each.  FP64 steps ping-pong through the CG r/p vectors; FP32
 // steps through the same memory viewed as floats.
@@ -304,6 +352,7 @@ __global__ void __launch_bounds__(ATHREADS, 2) async_kernel(AsyncDev a) {
     // ---------------- fine propagation v = F(xs_i) ----------------
     const bool ok = a.cn ? team_fine_cn(a, bar, xs, tv, ws, cgx + 4 * M, tb)
                     : a.f_prec == 32 ? team_fine<float>(a, bar, xs, tv, ws.r, ws.p, tb)
+                    : a.f_period > 0 ? team_fine_scaled(a, bar, xs, tv, ws.r, ws.p, tb)
                                      : team_fine<double>(a, bar, xs, tv, ws.r, ws.p, tb);
     if (!ok) break;
 
@@ -522,6 +571,18 @@ int run_async(pr_ctx* c, const pr_async_opts* o, double* lam, pr_stats* st, pr_e
   a.f_rtol = p.f_rtol;
   a.f_maxit = p.f_maxit;
   a.tcg_stride = cn ? 5 : 4;
+  a.f_period = 0;
+  if (!cn && !c->var_kappa && p.f_prec == 64 && p.f_steps > 1) {
+    const int R = scaled_period(c->fst.rx);
+    if (R > 0) {
+      const double rx = c->fst.rx;
+      a.f_period = R;
+      a.fsc = {c->fst.c0 / rx, 1.0, c->fst.ry / rx, c->fst.rz / rx};
+      a.f_sigma_R = std::pow(rx, R);
+      const int rem = p.f_steps % R;
+      a.f_sigma_last = std::pow(rx, rem == 0 ? R : rem);
+    }
+  }
   a.u0 = p.u0_dev;
   double* dp = static_cast<double*>(c->async_ws);
   a.ring = dp;

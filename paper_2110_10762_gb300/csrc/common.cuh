@@ -142,6 +142,9 @@ int cuda_fail(pr_ctx* c, cudaError_t e, const char* where);
 cudaError_t explicit_fine(pr_ctx* c, const double* in, double* out, int count, int steps,
                           int prec);
 cudaError_t build_var_coefficients(pr_ctx* c);
+// Steps between two returns to u in the scaled FP64 explicit form (0: use the
+// plain form); the batched kernel and the asynchronous kernel share it.
+int scaled_period(double rx);
 // One FP64 explicit step u' = S u on `count` states (S is symmetric, so this is
 // also the transposed step used by the adjoint).
 cudaError_t explicit_step64(pr_ctx* c, const double* in, double* out, int count);

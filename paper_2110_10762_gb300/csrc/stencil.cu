@@ -293,15 +293,6 @@ cudaError_t launch_step(const pr_ctx* c, const Tin* in, Tout* out, int count,
   return launch_step_mode<Tin, Tout, T, false, 0>(c, in, out, count, k, cv);
 }
 
-// Steps between two returns to u in the scaled form: sigma^-1 = rx^-R stays
-// below 1e100, so intermediate values stay within 1e100 of the input's
-// magnitude (FP64 range: inputs up to 1e200 in magnitude are safe).
-int scaled_period(double rx) {
-  if (!(rx > 0.0 && rx < 1.0)) return 0;
-  const double r = std::floor(100.0 / std::log10(1.0 / rx));
-  return r < 1.0 ? 1 : (r > 1e6 ? 1000000 : static_cast<int>(r));
-}
-
 // `steps` FP64 constant-kappa steps in the scaled form, ping-ponging between
 // `out` and c->tmp so that the last step writes `out`.
 cudaError_t scaled_fine64(pr_ctx* c, const double* in, double* out, int count, int steps) {
@@ -410,6 +401,15 @@ __global__ void to_float_kernel(const double* __restrict__ a, float* __restrict_
 }
 
 }  // namespace
+
+// Steps between two returns to u in the scaled form: sigma^-1 = rx^-R stays
+// below 1e100, so intermediate values stay within 1e100 of the input's
+// magnitude (FP64 range: inputs up to 1e200 in magnitude are safe).
+int scaled_period(double rx) {
+  if (!(rx > 0.0 && rx < 1.0)) return 0;
+  const double r = std::floor(100.0 / std::log10(1.0 / rx));
+  return r < 1.0 ? 1 : (r > 1e6 ? 1000000 : static_cast<int>(r));
+}
 
 cudaError_t build_var_coefficients(pr_ctx* c) {
   const Geom& g = c->g;
