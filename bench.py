@@ -73,10 +73,11 @@ def fp64_ops_per_lup(p, scaled=True):
     return 2.0 * dim + math.ceil(p["f_steps"] / R) / p["f_steps"]
 
 
-# Trapezoidal F in 2D/3D: per CG iteration and point, the operator (1 DMUL + d DADD +
-# d DFMA) plus 5 DFMA (p.q, x, r, r.r, p); per fine step and point, the right-hand side
-# (explicit form, same count as the operator) plus the start residual and its norms (3).
-CN_OPS_PER_CG_POINT = {2: 10, 3: 12}
+# Trapezoidal F in 2D/3D: per CG iteration and point, the operator scaled by 1/R_x
+# (d DADD + d DFMA) plus 5 DFMA (p.q, x, r, r.r, p); per fine step and point, the
+# right-hand side (explicit form: 1 DMUL + d DADD + d DFMA), the start residual
+# (the unscaled operator and b - Ax) and its two norms.
+CN_OPS_PER_CG_POINT = {2: 9, 3: 11}
 CN_OPS_PER_LUP = {2: 13, 3: 17}
 NOMINAL_FP64_OPS = 625.0  # G FP64-pipe ops/s: 1.25 TFLOP/s nominal / 2 flops per DFMA
 # DRAM bytes (read + write) per cell update of the dominant kernel, from one ncu capture

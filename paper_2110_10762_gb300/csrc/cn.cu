@@ -121,9 +121,33 @@ void cn_free(pr_ctx* c) {
   c->cn_teams = c->cn_cap = 0;
 }
 
+#ifndef PR_CN_L2_FRACTION
+#define PR_CN_L2_FRACTION 0.8
+#endif
+
+// Teams for a batch of `count` slices: as many as the batch and the workspace
+// allow, but no more than keep the teams' six CG vectors within about 80% of
+// L2 (beyond that every CG iteration streams its vectors from HBM and the
+// kernel is bound by HBM as much as by the FP64 pipe); the slices then run in
+// waves, and the team count is evened out over the waves.
+int cn_team_count(const pr_ctx* c, int count) {
+  int T = count < c->cn_teams ? count : c->cn_teams;
+  int l2 = 0;
+  if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, c->device) != cudaSuccess || l2 <= 0)
+    return T;
+  const double per_team = 6.0 * (double)c->g.M * sizeof(double);
+  int t_l2 = (int)(PR_CN_L2_FRACTION * l2 / per_team);
+  if (t_l2 < 1) t_l2 = 1;
+  if (t_l2 < T) {
+    const int waves = (count + t_l2 - 1) / t_l2;
+    T = (count + waves - 1) / waves;
+  }
+  return T;
+}
+
 cudaError_t cn_fine(pr_ctx* c, const double* in, double* out, int count) {
   if (count <= 0) return cudaSuccess;
-  const int T = count < c->cn_teams ? count : c->cn_teams;
+  const int T = cn_team_count(c, count);
   const int C = c->cn_cap / T;
   cudaError_t e = cudaMemsetAsync(c->cn_bar, 0, (size_t)T * sizeof(unsigned long long), c->stream);
   if (e != cudaSuccess) return e;
