@@ -107,6 +107,8 @@ def parse():
     ap.add_argument("--chunks", type=int, default=8, help="slice chunks per pipelined F batch")
     ap.add_argument("--g-cheb", type=int, default=0,
                     help="coarse CG preconditioned by this many FP32 Chebyshev steps (0 = plain CG)")
+    ap.add_argument("--ctas-per-slice", type=int, default=0,
+                    help="async workloads: CTAs per slice team (0 = automatic)")
     ap.add_argument("--lazy", action="store_true",
                     help="async workloads: skip re-updates that a newer input will supersede")
     ap.add_argument("--cg-bps", type=int, default=0,
@@ -345,7 +347,7 @@ def run_async_workload(args, local):
         unit_ns = t_ms * 1e6 / p["f_steps"]
         delays = torch.from_numpy(delay_table(N, 64, seed=p["delay_seed"])).cuda()
     opts = pr.make_async_opts(timeout_s=300.0, delays=delays, delay_unit_ns=unit_ns,
-                              lazy=args.lazy)
+                              lazy=args.lazy, ctas_per_slice=args.ctas_per_slice)
     if args.profile:
         code, st, log = pr.parareal_run_async(ctx, opts, lam, log_cap=1 << 20)
         torch.cuda.synchronize()
@@ -402,7 +404,7 @@ def run_async_workload(args, local):
            "config": {"workload": WORKLOADS[args.workload], "grid": list(p["n"]), "N": N,
                       "f_steps": p["f_steps"], "tol": p["tol"],
                       "delay_unit_ns": unit_ns, "delays": delays is not None,
-                      "lazy": bool(args.lazy)},
+                      "lazy": bool(args.lazy), "ctas_per_slice": args.ctas_per_slice},
            "async": {"status": int(code), "time_to_tol_ms": t_async, "kappa": st.iterations,
                      "events": st.events, "cg_iterations": st.cg_iterations,
                      "fine_cg_iterations": st.fine_cg_iterations,

@@ -115,7 +115,9 @@ typedef struct pr_async_opts {
                                slice i's e-th update, in units of delay_unit_ns */
   int delay_cols;           /* columns of delays_dev (events beyond it use column e % delay_cols) */
   double delay_unit_ns;     /* duration of one delay unit */
-  int ctas_per_slice;       /* CTAs cooperating on one slice update (0 = automatic) */
+  int ctas_per_slice;       /* CTAs cooperating on one slice update (0 = automatic: about as
+                               many teams as their CG working sets fit in L2, each team
+                               owning slices round-robin; at most 8 CTAs when all fit) */
   int quiescence;           /* 1: ignore tol and run until no slice can change */
   int lazy;                 /* 1: after an update whose fine input was older than its coarse
                                input, re-update only when a newer predecessor version
