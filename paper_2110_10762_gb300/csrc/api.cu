@@ -7,9 +7,18 @@
 #include <algorithm>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 
 namespace pr {
+
+// NVTX range for the duration of a scope (timeline tools show the phases of
+// the drivers; without an attached tool the calls are no-ops).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 int fail(pr_ctx* c, int code, const std::string& msg) {
   if (c) c->err = msg;
@@ -422,6 +431,7 @@ int parareal_run_sync(pr_ctx* c, double* lam, pr_stats* st) {
   // device, so it cannot overlap the coarse sweep: plain schedule
   const bool cn_grid = c->prob.f_scheme == PR_CRANK_NICOLSON && c->g.dim > 1;
   if (c->opt_pipeline && !cn_grid) return run_sync_pipelined(c, lam, st);
+  NvtxRange range_all("parareal_run_sync");
   cn_take_iterations(c);
   const pr_problem& p = c->prob;
   const long long M = c->g.M;
@@ -435,6 +445,7 @@ int parareal_run_sync(pr_ctx* c, double* lam, pr_stats* st) {
   PR_CUDA(c, cudaEventRecord(c->ev[0], c->stream));
   PR_CUDA(c, cudaMemcpyAsync(lam, p.u0_dev, M * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
   // Predictor (Algorithm 1, first lines): w_i^0 = G(lam_{i-1}^0), lam_i^0 = w_i^0.
+  nvtxRangePushA("predictor");
   PR_CUDA(c, cudaMemsetAsync(c->cg_iters_dev, 0, (N + 1) * sizeof(int), c->stream));
   for (int i = 1; i <= N; ++i) {
     double* wi = c->w + (i - 1) * M;
@@ -460,6 +471,7 @@ int parareal_run_sync(pr_ctx* c, double* lam, pr_stats* st) {
                              cudaMemcpyDeviceToHost, c->stream));
   PR_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
   PR_CUDA(c, cudaStreamSynchronize(c->stream));
+  nvtxRangePop();
   cudaEventElapsedTime(&t_g, c->ev[0], c->ev[1]);
   for (int i = 1; i <= N; ++i) {
     S.cg_iterations += iters[i];
@@ -473,8 +485,12 @@ int parareal_run_sync(pr_ctx* c, double* lam, pr_stats* st) {
     const int count = N - k;
     // fine propagation of every active slice at once: v_i = F(lam_{i-1}^k), i = k+1..N
     PR_CUDA(c, cudaEventRecord(c->ev[2], c->stream));
-    PR_CUDA(c, fine_batch(c, lam + (size_t)k * M, c->v + (size_t)k * M, count));
+    {
+      NvtxRange r("fine batch");
+      PR_CUDA(c, fine_batch(c, lam + (size_t)k * M, c->v + (size_t)k * M, count));
+    }
     PR_CUDA(c, cudaEventRecord(c->ev[3], c->stream));
+    nvtxRangePushA("coarse sweep");
     S.launches += p.f_scheme == PR_EXPLICIT_EULER ? p.f_steps : 1;
     S.fine_lups += (long long)count * M * p.f_steps;
     // sequential coarse sweep with the fused correction and increment
@@ -511,6 +527,7 @@ int parareal_run_sync(pr_ctx* c, double* lam, pr_stats* st) {
         S.launches += 1;
       }
     }
+    nvtxRangePop();
     PR_CUDA(c, cudaEventRecord(c->ev[4], c->stream));
     PR_CUDA(c, cudaMemcpyAsync(dbits.data(), c->delta_dev, N * sizeof(unsigned long long),
                                cudaMemcpyDeviceToHost, c->stream));

@@ -108,6 +108,28 @@ def test_async_with_injected_delays():
         assert e.t_end >= e.t_start + int(dly * 20000.0) - 1
 
 
+def test_async_one_slice_delayed_far_beyond_the_others():
+    """An extreme delay schedule: every publication of slice 3 becomes visible only
+    after 200 delay units, the others at once.  The run still terminates (quiescence),
+    its log replays, and the result is the serial fine solution."""
+    p = case("heat2d_explicit", tol=1e-9)
+    delays = np.zeros((p["N"], 8), dtype=np.int32)
+    delays[2, :] = 200
+    with Ctx(p) as c:
+        d = torch().from_numpy(delays).cuda()
+        code, st, log, lam = run_async(c, timeout_s=60.0, delays=d, delay_unit_ns=20000.0,
+                                       quiescence=True)
+    assert code == pr.PR_OK and st.converged
+    check_log(log, p["N"])
+    rep = async_replay(p, events_of(log))
+    assert rel_l2(lam, rep.lam) < FP64_TOL
+    assert rel_l2(lam, serial_fine(p)) < FP64_TOL
+    # the delayed slice's versions became visible 200 units after their start
+    for e in log:
+        if e.slice == 3:
+            assert e.t_end >= e.t_start + 200 * 20000 - 1
+
+
 @pytest.mark.parametrize("quiescence", [False, True])
 def test_async_lazy_policy(quiescence):
     """Skipping superseded re-updates keeps replay parity and the quiescent fixed point."""

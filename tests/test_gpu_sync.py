@@ -383,3 +383,28 @@ def test_notconv_status_when_max_iter_stops_early():
         lam = c.lam()
         code, st = pr.parareal_run_sync(c.ctx, lam)
         assert code == pr.PR_ENOTCONV and st.iterations == 2 and not st.converged
+
+
+@pytest.mark.parametrize("case", ["2d_const", "2d_var", "3d_const", "3d_var"])
+def test_fine_and_coarse_are_symmetric(case):
+    """Dot-product tests <F x, y> = <x, F y> and <G x, y> = <x, G y> of the GPU
+    propagators (F = S^n_f and G = (I + dT A)^-1 are symmetric; the adjoint relies on it)."""
+    p = CASES[case]()
+    p["f_prec"] = 64
+    p["g_rtol"] = 1e-14
+    rng = np.random.default_rng(19)
+    shape = tuple(reversed(p["n"]))
+    x, y = rng.standard_normal(shape), rng.standard_normal(shape)
+    with Ctx(p) as c:
+        outs = {}
+        for name, v in (("x", x), ("y", y)):
+            f = torch().empty(c.M, dtype=torch().float64, device="cuda")
+            g = torch().empty(c.M, dtype=torch().float64, device="cuda")
+            pr.parareal_fine(c.ctx, dev(v), f, 1)
+            pr.parareal_coarse(c.ctx, dev(v), None, g)
+            outs[name] = (host(f), host(g))
+    fx, gx = outs["x"]
+    fy, gy = outs["y"]
+    xv, yv = x.reshape(-1), y.reshape(-1)
+    for a, b in ((fx @ yv, xv @ fy), (gx @ yv, xv @ gy)):
+        assert abs(a - b) <= 1e-12 * max(abs(a), np.linalg.norm(xv) * np.linalg.norm(yv) * 1e-3)
