@@ -9,21 +9,25 @@ iterations, no early stop; Eq. (11)):
                 lambda_i^{k+1} = w_i^{k+1} + v_i^k - w_i^k
         else:   lambda_i^{k+1} = lambda_i^k
     L = 1/2 ||lambda_N^K - u_obs||^2 (the caller supplies dL/dlambda_N).
-F = S^{n_f} with S = I - dt A_kappa and G = (I + dT A_kappa)^{-1} are
-symmetric, so F^T = F and G^T = G.  G is taken as the exact solve (CG to the
-problem's g_rtol, which callers set tight).
+F = S^{n_f} with S = I - dt A_kappa (explicit) or S = (I + dt A_kappa)^{-1}
+(implicit, 1D) and G = (I + dT A_kappa)^{-1} are symmetric, so F^T = F and
+G^T = G.  G is taken as the exact solve (CG to the problem's g_rtol, which
+callers set tight, or Thomas in 1D).
 
 Diffusivity derivative: <a, A_kappa u> = sum_faces h^-2 kappa_f (a_p-a_q)(u_p-u_q)
 with kappa_f = (kappa_p + kappa_q)/2, so each face adds h^-2 (Da)_f (Du)_f / 2 to
 both of its nodes (boundary-ring nodes included).  Then
-    d<abar, S^n x>/dkappa = -dt sum_j facegrad(S^{n-1-j} abar, S^j x)
+    d<abar, S^n x>/dkappa = -dt sum_j facegrad(S^{n-1-j} abar, S^j x)          (explicit)
+    d<abar, S^n x>/dkappa = -dt sum_j facegrad(S^{n-j} abar, S^{j+1} x)        (implicit)
     d<wbar, G b>/dkappa   = -dT facegrad(G wbar, G b).
+(implicit: u_{j+1} = S u_j with S = (I + dt A)^{-1}, whose derivative is
+-S dt (dA/dkappa) S.)
 """
 from __future__ import annotations
 
 import numpy as np
 
-from .heat import Propagators, _h_of_axis, explicit_euler
+from .heat import Propagators, _h_of_axis, explicit_euler, implicit_euler_1d
 
 
 def face_grad(a: np.ndarray, u: np.ndarray, h, ring_shape) -> np.ndarray:
@@ -66,6 +70,17 @@ class _Ops:
     def F_adj(self, x, abar, want_kappa):
         """(F^T abar, d<abar, F x>/dkappa) with the fine states recomputed from x."""
         P = self.P
+        if P.f_scheme == "implicit":
+            states = [x.reshape(self.shape)]
+            for _ in range(P.f_steps):
+                states.append(implicit_euler_1d(states[-1], P.dt, P.h, P.kappa, 1))
+            a = abar.reshape(self.shape)
+            gk = np.zeros(self.ring) if want_kappa else None
+            for j in range(P.f_steps - 1, -1, -1):
+                a = implicit_euler_1d(a, P.dt, P.h, P.kappa, 1)      # S^T = S
+                if want_kappa:
+                    gk -= P.dt * face_grad(a, states[j + 1], P.h, self.ring)
+            return a.reshape(-1), gk
         states = [x.reshape(self.shape)]
         for _ in range(P.f_steps - 1):
             states.append(explicit_euler(states[-1], P.dt, P.h, P.kappa, 1))
@@ -94,8 +109,8 @@ def adjoint_sync(prob: dict, dL_dlamN, K: int, u0=None, kappa="from_prob"):
     None for constant kappa, lam_N^K).  Explicit fine propagator only.
     """
     ops = _Ops(prob, kappa)
-    if ops.P.f_scheme != "explicit":
-        raise ValueError("adjoint oracle covers the explicit fine propagator")
+    if ops.P.f_scheme not in ("explicit", "implicit") or ops.P.g_steps != 1:
+        raise ValueError("adjoint oracle covers explicit and 1D implicit fine propagators, one coarse step")
     want_k = ops.P.kappa is not None
     u0 = prob["u0"] if u0 is None else u0
     N = int(prob["N"])

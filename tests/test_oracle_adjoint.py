@@ -169,3 +169,38 @@ def test_async_adjoint_at_quiescence_is_adjoint_of_serial_fine():
     for _ in range(p["N"]):
         ref = P.F(ref)
     np.testing.assert_allclose(gu0, ref, rtol=0, atol=1e-10 * np.max(np.abs(ref)))
+
+
+# ------------------------------------------- 1D implicit fine steps, Thomas coarse solve
+def prob1d(var=True, N=4, f_steps=5, n=(13,), seed=0):
+    rng = np.random.default_rng(seed)
+    h = (1.0 / (n[0] + 1),)
+    kap = np.exp(0.4 * rng.standard_normal(n[0] + 2)) if var else None
+    return dict(dim=1, n=n, h=h, N=N, f_steps=f_steps, dt=2.0 * h[0] ** 2, f_scheme="implicit",
+                g_solver="thomas", g_rtol=0.0, kappa=kap, u0=rng.standard_normal(n), tol=0.0)
+
+
+def test_implicit_1d_adjoint_transposition_and_differences():
+    """Tridiagonal solves run backward: <J v, y> = <v, J^T y> for u0, and central
+    differences for kappa and u0."""
+    p = prob1d(seed=31)
+    K = 2
+    rng = np.random.default_rng(32)
+    v, y = rng.standard_normal(p["n"]), rng.standard_normal(p["n"])
+    _, Jv = loss_and_forward(p, K, np.zeros(p["n"]), u0=v)
+    gu0, _, _ = adjoint_sync(p, y, K, u0=v)
+    lhs, rhs = float(Jv @ y), float(np.sum(v * gu0))
+    assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), 1.0)
+    u_obs = rng.standard_normal(p["n"])
+    L0, lamN = loss_and_forward(p, K, u_obs)
+    gu0, gk, _ = adjoint_sync(p, lamN - u_obs, K)
+    for trial in range(3):
+        d = rng.standard_normal(p["kappa"].shape)
+        eps = 1e-6 * np.max(np.abs(p["kappa"]))
+        Lp, _ = loss_and_forward(dict(p, kappa=p["kappa"] + eps * d), K, u_obs)
+        Lm, _ = loss_and_forward(dict(p, kappa=p["kappa"] - eps * d), K, u_obs)
+        assert np.isclose(np.sum(gk * d), (Lp - Lm) / (2 * eps), rtol=1e-6, atol=1e-12), trial
+        du = rng.standard_normal(p["n"])
+        Lp, _ = loss_and_forward(p, K, u_obs, u0=p["u0"] + 1e-6 * du)
+        Lm, _ = loss_and_forward(p, K, u_obs, u0=p["u0"] - 1e-6 * du)
+        assert np.isclose(np.sum(gu0 * du), (Lp - Lm) / 2e-6, rtol=1e-6)
