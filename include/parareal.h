@@ -190,7 +190,9 @@ int parareal_correct(pr_ctx* ctx, const double* w_new_dev, const double* v_dev,
 
 /* Discrete adjoint (reverse mode) of K synchronous iterations (Algorithm 1
  * with the prefix frozen, no early stop) of the trajectory map u0 -> lam_N^K,
- * G taken as the exact solve (I + dT A)^{-1} (CG to g_rtol).  Given
+ * G taken as the exact solve (I + dT A)^{-1} (CG to g_rtol, or the Thomas
+ * step in 1D).  Fine steps: FP64 explicit (any dimension) or 1D implicit
+ * (the tridiagonal solves run backward: S^-1 is symmetric); one coarse step.  Given
  * dL/dlam_N (M doubles), writes grad_u0_dev (M doubles) and, if non-NULL,
  * grad_kappa_dev (prod(n+2) doubles, one per node including the ring).
  * Fine states are recomputed from slice-boundary checkpoints. */

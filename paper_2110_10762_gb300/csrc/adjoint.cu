@@ -104,8 +104,13 @@ long long ring_count(const Geom& g) {
 
 int run_adjoint(pr_ctx* c, const double* gN, int K, double* grad_u0, double* grad_kappa) {
   const pr_problem& p = c->prob;
-  if (p.f_scheme != PR_EXPLICIT_EULER || p.g_solver != PR_SOLVER_CG || p.f_prec != 64)
-    return fail(c, PR_EINVAL, "adjoint needs the FP64 explicit fine scheme and the CG coarse solver");
+  // explicit F (any dimension) or implicit F (1D, tridiagonal solves); G by CG
+  // or, in 1D, by one Thomas step
+  const bool implicit = p.f_scheme == PR_IMPLICIT_EULER;
+  const bool thomas = p.g_solver == PR_SOLVER_THOMAS;
+  if ((p.f_scheme != PR_EXPLICIT_EULER && !implicit) || p.f_prec != 64 || p.g_steps != 1)
+    return fail(c, PR_EINVAL,
+                "adjoint needs FP64 explicit or 1D implicit fine steps and one coarse step");
   const Geom& g = c->g;
   const long long M = g.M;
   const int N = p.N, nf = p.f_steps;
@@ -113,7 +118,9 @@ int run_adjoint(pr_ctx* c, const double* gN, int K, double* grad_u0, double* gra
   if (grad_kappa && !var) return fail(c, PR_EINVAL, "grad_kappa needs a variable-kappa problem");
   const long long Mr = ring_count(g);
   const size_t traj = (size_t)(K + 1) * (N + 1) * M;
-  const size_t words = 4 * traj + (size_t)std::max(nf - 1, 1) * N * M + 2 * (size_t)N * M + M +
+  // recomputed fine states: u_1..u_{nf-1} (explicit) or u_1..u_nf (implicit)
+  const size_t nstates = (size_t)std::max(implicit ? nf : nf - 1, 1);
+  const size_t words = 4 * traj + nstates * N * M + 2 * (size_t)N * M + M +
                        (var ? (size_t)Mr : 0);
   const size_t bytes = words * sizeof(double);
   if (c->adj_ws_bytes < bytes) {
@@ -129,7 +136,7 @@ int run_adjoint(pr_ctx* c, const double* gN, int K, double* grad_u0, double* gra
   double* lb = wv + traj;
   double* wb = lb + traj;
   double* states = wb + traj;
-  double* abuf0 = states + (size_t)std::max(nf - 1, 1) * N * M;
+  double* abuf0 = states + nstates * N * M;
   double* abuf1 = abuf0 + (size_t)N * M;
   double* zbuf = abuf1 + (size_t)N * M;
   double* kbar = var ? zbuf + M : nullptr;
@@ -140,6 +147,7 @@ int run_adjoint(pr_ctx* c, const double* gN, int K, double* grad_u0, double* gra
     return cudaGetLastError();
   };
   auto G = [&](const double* b, double* out) {
+    if (thomas) return tri_solve_steps(c, &c->tri_g, b, out, 1, 1);
     CgArgs a{};
     a.b = b;
     a.x0 = b;
@@ -148,12 +156,22 @@ int run_adjoint(pr_ctx* c, const double* gN, int K, double* grad_u0, double* gra
     a.mode = CG_PLAIN;
     return cg_solve(c, a);
   };
+  // one fine step on `count` states: explicit S or the implicit solve S^-1 (both symmetric)
+  auto step = [&](const double* in, double* out, int count) {
+    return implicit ? tri_solve_steps(c, &c->tri_f, in, out, count, 1)
+                    : explicit_step64(c, in, out, count);
+  };
   unsigned long long* dscratch = c->delta_dev;
 
   // ------------------------------------------------ forward with checkpoints
   PR_CUDA(c, cudaMemcpyAsync(L(lam, 0, 0), p.u0_dev, M * sizeof(double), cudaMemcpyDeviceToDevice,
                              c->stream));
   for (int i = 1; i <= N; ++i) {
+    if (thomas) {
+      PR_CUDA(c, G(L(lam, 0, i - 1), L(wv, 0, i)));
+      PR_CUDA(c, vec_copy(c, L(lam, 0, i), L(wv, 0, i), M));
+      continue;
+    }
     CgArgs a{};
     a.b = L(lam, 0, i - 1);
     a.x0 = a.b;
@@ -168,10 +186,14 @@ int run_adjoint(pr_ctx* c, const double* gN, int K, double* grad_u0, double* gra
                                cudaMemcpyDeviceToDevice, c->stream));
     PR_CUDA(c, cudaMemcpyAsync(L(wv, k + 1, 0), L(wv, k, 0), (size_t)(N + 1) * M * sizeof(double),
                                cudaMemcpyDeviceToDevice, c->stream));
-    PR_CUDA(c, explicit_fine(c, L(lam, k, k), c->v + (size_t)k * M, N - k, nf, 64));
+    PR_CUDA(c, fine_apply(c, L(lam, k, k), c->v + (size_t)k * M, N - k));
     for (int i = k + 1; i <= N; ++i) {
       double* vi = c->v + (size_t)(i - 1) * M;
-      if (i - 1 > k) {
+      if (i - 1 > k && thomas) {
+        PR_CUDA(c, G(L(lam, k + 1, i - 1), L(wv, k + 1, i)));
+        PR_CUDA(c, cudaMemsetAsync(dscratch, 0, sizeof(unsigned long long), c->stream));
+        PR_CUDA(c, correct(c, L(wv, k + 1, i), vi, L(wv, k, i), L(lam, k + 1, i), dscratch));
+      } else if (i - 1 > k) {
         CgArgs a{};
         a.b = L(lam, k + 1, i - 1);
         a.x0 = L(wv, k + 1, i);
@@ -216,21 +238,33 @@ int run_adjoint(pr_ctx* c, const double* gN, int K, double* grad_u0, double* gra
     // batched fine adjoint for i = k+1..N: inputs lambda_{i-1}^k, vbar_i = lambar_i^{k+1}
     const int count = N - k;
     const double* x0 = L(lam, k, k);
-    for (int j = 1; j < nf; ++j) {
+    // states u_j (j >= 1) recomputed from the checkpoint u_0 = lambda_{i-1}^k
+    for (int j = 1; j <= (int)nstates && (implicit || j < nf); ++j) {
       const double* src = j == 1 ? x0 : states + (size_t)(j - 2) * N * M;
-      PR_CUDA(c, explicit_step64(c, src, states + (size_t)(j - 1) * N * M, count));
+      PR_CUDA(c, step(src, states + (size_t)(j - 1) * N * M, count));
     }
     PR_CUDA(c, cudaMemcpyAsync(abuf0, L(lb, k + 1, k + 1), (size_t)count * M * sizeof(double),
                                cudaMemcpyDeviceToDevice, c->stream));
     double* a = abuf0;
     double* b = abuf1;
     for (int j = nf - 1; j >= 0; --j) {
-      const double* uj = j == 0 ? x0 : states + (size_t)(j - 1) * N * M;
-      if (var) {
-        facegrad_kernel<<<blocks, 256, 0, c->stream>>>(g, kbar, a, uj, count, -c->dt);
-        PR_CUDA(c, cudaGetLastError());
+      if (!implicit) {
+        // explicit: d<a_{j+1}, S u_j> gives -dt facegrad(a_{j+1}, u_j); a_j = S a_{j+1}
+        const double* uj = j == 0 ? x0 : states + (size_t)(j - 1) * N * M;
+        if (var) {
+          facegrad_kernel<<<blocks, 256, 0, c->stream>>>(g, kbar, a, uj, count, -c->dt);
+          PR_CUDA(c, cudaGetLastError());
+        }
+        PR_CUDA(c, step(a, b, count));
+      } else {
+        // implicit: a_j = S^-1 a_{j+1}, then -dt facegrad(a_j, u_{j+1})
+        PR_CUDA(c, step(a, b, count));
+        if (var) {
+          facegrad_kernel<<<blocks, 256, 0, c->stream>>>(g, kbar, b, states + (size_t)j * N * M,
+                                                          count, -c->dt);
+          PR_CUDA(c, cudaGetLastError());
+        }
       }
-      PR_CUDA(c, explicit_step64(c, a, b, count));
       std::swap(a, b);
     }
     PR_CUDA(c, axpy(L(lb, k, k), a, 1.0, (long long)count * M));

@@ -260,3 +260,18 @@ def test_async_adjoint_rejects_invalid_logs():
             with pytest.raises(pr.PararealError) as e:
                 pr.parareal_adjoint_async(c.ctx, as_events(evs), g, gu0)
             assert e.value.code == pr.PR_EINVAL
+
+
+@pytest.mark.parametrize("K", [1, 3])
+def test_adjoint_1d_implicit_thomas(K):
+    """Tridiagonal solves run backward: 1D implicit fine steps and the Thomas coarse
+    step, variable kappa, against the oracle's adjoint."""
+    p = preset("heat1d_thomas", "small")
+    rng = np.random.default_rng(71)
+    p["kappa"] = np.exp(0.4 * rng.standard_normal(p["n"][0] + 2))
+    p["tol"] = 0.0
+    g = rng.standard_normal(tuple(reversed(p["n"])))
+    ref_u0, ref_k, _ = adjoint_sync(p, g, K)
+    got_u0, got_k = gpu_adjoint(p, g, K)
+    assert rel_l2(got_u0, ref_u0) < 1e-12
+    assert rel_l2(got_k, ref_k) < 1e-11
