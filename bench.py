@@ -617,7 +617,9 @@ def run_ours(args, world, rank, local):
     fine_glups = lups_r / (t_fine / 1e3) / 1e9
     if is_mixed:
         roof = {"bound": "hbm", "achieved": alg_bytes / (t_fine / 1e3) / 1e9, "peak": hbm_peak,
-                "unit": "GB/s", "traffic": None, "kernel": "step3d<float>",
+                "unit": "GB/s", "traffic": None,
+                "kernel": ("step3d_tma (TMA-fed FP32 steps; first/last step step3d_v4)"
+                           if p["n"][0] % 4 == 0 and p.get("kappa") is None else "step3d_v4<float>"),
                 "peak_kind": peak_kind}
     elif is_cn:
         f_its = sum(s["fine_cg_iterations"] for s in roof_stats)

@@ -37,6 +37,7 @@ bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 void free_problem(pr_ctx* c) {
   void* ptrs[] = {c->fcoef, c->fcoef32, c->gcoef, c->fsys0, c->v, c->w, c->tmp, c->f32a, c->f32b,
+                  c->tma_err,
                   c->cg_x, c->cg_r, c->cg_p, c->cg_q, c->cg_part, c->cg_iters_dev,
                   c->delta_dev, c->u0_stage, c->lam_stage, c->async_ws, c->adj_ws};
   for (void* p : ptrs)
@@ -47,6 +48,8 @@ void free_problem(pr_ctx* c) {
   c->fsys0 = nullptr;
   c->v = c->w = c->tmp = nullptr;
   c->f32a = c->f32b = nullptr;
+  c->tma_err = nullptr;
+  c->tma_ok = false;
   c->cg_x = c->cg_r = c->cg_p = c->cg_q = c->cg_part = nullptr;
   c->cg_iters_dev = nullptr;
   c->delta_dev = nullptr;
@@ -272,6 +275,7 @@ int parareal_set_problem(pr_ctx* c, const pr_problem* pin) {
     free_problem(c);
     return cuda_fail(c, e, "tridiagonal tables");
   }
+  tma_prepare(c);  // optional: the TMA-fed FP32 steps when their tensor maps encode
   if (p.g_solver == PR_SOLVER_CG) chk(coarse_bounds(c));
   if (p.g_solver == PR_SOLVER_CG && c->opt_g_cheb) chk(cheb_alloc(c));
   if (e != cudaSuccess) {

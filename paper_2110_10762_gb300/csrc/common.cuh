@@ -83,6 +83,10 @@ struct pr_ctx {
   double* tmp = nullptr;     // N*M ping-pong for explicit F
   float* f32a = nullptr;     // N*M FP32 ping-pong (mixed form)
   float* f32b = nullptr;
+  // TMA-fed FP32 3D steps (tma_stencil.cu): tensor maps of f32a / f32b
+  bool tma_ok = false;
+  alignas(64) unsigned char tma_map[2][128] = {};
+  int* tma_err = nullptr;
   double* cg_x = nullptr;    // CG vectors (M each)
   double* cg_r = nullptr;
   double* cg_p = nullptr;
@@ -159,6 +163,11 @@ cudaError_t cn_fine(pr_ctx* c, const double* in, double* out, int count);
 unsigned long long cn_take_iterations(pr_ctx* c);
 // F on `count` consecutive states with the problem's fine scheme (api.cu).
 cudaError_t fine_apply(pr_ctx* c, const double* in, double* out, int count);
+
+// ---- TMA-fed FP32 3D step (tma_stencil.cu)
+bool tma_prepare(pr_ctx* c);
+cudaError_t tma_step(pr_ctx* c, const float* src, float* dst, int count);
+int tma_take_error(pr_ctx* c);
 
 // ---- tridiagonal partition solver (tridiag.cu)
 // cn: trapezoidal-rule tables (r is then dt/(2 h^2); each solve is preceded by

@@ -479,11 +479,14 @@ cudaError_t explicit_fine(pr_ctx* c, const double* in, double* out, int count, i
   const float* src = c->f32a;
   for (int s = 1; s < steps - 1; ++s) {
     float* dst = (src == c->f32a) ? c->f32b : c->f32a;
-    e = launch_step<float, float, float>(c, src, dst, count, c->fvar32);
+    e = c->tma_ok ? tma_step(c, src, dst, count)
+                  : launch_step<float, float, float>(c, src, dst, count, c->fvar32);
     if (e != cudaSuccess) return e;
     src = dst;
   }
-  return launch_step<float, double, float>(c, src, out, count, c->fvar32);
+  e = launch_step<float, double, float>(c, src, out, count, c->fvar32);
+  if (e == cudaSuccess && c->tma_ok && steps > 2 && tma_take_error(c)) e = cudaErrorTimeout;
+  return e;
 }
 
 }  // namespace pr

@@ -1,0 +1,257 @@
+// FP32 3D constant-kappa explicit step fed by the Tensor Memory Accelerator
+// (the HBM-bound middle steps of the mixed form, §3.1 F run in FP32).
+//
+// A block owns a 64 x 16 column of the grid for 32 z planes and streams z
+// (2.5D): one elected thread issues cp.async.bulk.tensor loads of whole planes
+// of the tile plus halo (72 x 18 floats: the x halo is 4 wide so that every
+// load starts on a 16-byte boundary) into a four-stage shared-memory ring,
+// each stage completed by its own mbarrier (transaction bytes).  Loads run two
+// planes ahead of the plane being computed.  Outside the grid the copy engine
+// fills zeros, which are exactly the Dirichlet boundary values, so the compute
+// loop has no boundary branches.  Each thread computes 4 consecutive x points
+// (one float4 from shared memory, x neighbours at the ends) and stores them
+// with one 16-byte store.
+//
+// Every mbarrier wait is bounded; on expiry the block records an error word,
+// waits (again bounded) for its own loads still in flight, and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "common.cuh"
+
+namespace pr {
+
+namespace {
+
+constexpr int TTX = 64, TTY = 16;          // output tile
+constexpr int TZC = 32;                   // z planes per block
+constexpr int TST = 4;                    // ring stages
+constexpr int TPX = TTX + 8, TPY = TTY + 2;  // staged plane
+constexpr int TPLANE = TPX * TPY;            // floats per staged plane
+constexpr unsigned TBYTES = TPLANE * sizeof(float);
+// stage pitch rounded up to 128 bytes, so that every stage starts 128-byte aligned
+constexpr int TSTRIDE = (int)(((TBYTES + 127) / 128) * 128 / sizeof(float));
+constexpr int TMA_THREADS = (TTX / 4) * TTY;  // 256
+constexpr int WAIT_SPINS = 1 << 22;
+
+struct TmaArgs {
+  int nx, ny, nz, zchunks;
+  long long M;
+  float c0, rx, ry, rz;
+  float* out;
+  int* err;
+};
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// Bounded wait for the completion of phase `parity` of a stage barrier.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  for (int i = 0; i < WAIT_SPINS; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (i > 32) __nanosleep(64);
+  }
+  return false;
+}
+
+// Tile load of plane (x, y, z, slice) coordinates into shared memory.
+__device__ __forceinline__ void tma_load_plane(float* dst, const CUtensorMap* map, int x, int y,
+                                               int z, int s, unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(s),
+      "r"(smem_addr(bar))
+      : "memory");
+}
+
+__global__ void __launch_bounds__(TMA_THREADS) step3d_tma(const __grid_constant__ CUtensorMap src,
+                                                          TmaArgs a) {
+  __shared__ __align__(128) float stage[TST][TSTRIDE];
+  __shared__ __align__(8) unsigned long long bar[TST];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int slice = blockIdx.z / a.zchunks;
+  const int z0 = (blockIdx.z - slice * a.zchunks) * TZC;
+  const int zend = min(z0 + TZC, a.nz);
+  const int nload = zend - z0 + 2;  // planes z0-1 .. zend, load index L = plane - (z0-1)
+  const int x0 = blockIdx.x * TTX, y0 = blockIdx.y * TTY;
+  if (tid == 0) {
+#pragma unroll
+    for (int s = 0; s < TST; ++s) mbar_init(&bar[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](int L) {
+    const int s = L % TST;
+    mbar_arrive_expect_tx(&bar[s], TBYTES);
+    tma_load_plane(stage[s], &src, x0 - 4, y0 - 1, z0 - 1 + L, slice, &bar[s]);
+  };
+  if (tid == 0)
+    for (int L = 0; L < TST && L < nload; ++L) issue(L);
+  int issued = TST < nload ? TST : nload;  // loads issued so far (uniform: only thread 0 issues)
+  int waited = 0;                          // loads 0..waited-1 completed
+  bool ok = true, aborted = false;
+  const float c0 = a.c0, rx = a.rx, ry = a.ry, rz = a.rz;
+  const long long plane = (long long)a.nx * a.ny;
+  float* out = a.out + (long long)slice * a.M;
+  const int gx = x0 + 4 * tx, gy = y0 + ty;
+  const bool inside = gx < a.nx && gy < a.ny;
+  const int c = (ty + 1) * TPX + 4 + 4 * tx;  // this thread's first point in a stage
+  for (int zi = z0; zi < zend; ++zi) {
+    const int L = zi - z0 + 1;  // load index of the output plane
+    while (ok && waited <= L + 1) {
+      ok = mbar_wait(&bar[waited % TST], (waited / TST) & 1);
+      if (ok) ++waited;
+    }
+    if (__syncthreads_or(!ok)) {  // block-uniform decision
+      aborted = true;
+      break;
+    }
+    if (inside) {
+      const float* Pm = stage[(L - 1) % TST];
+      const float* Pc = stage[L % TST];
+      const float* Pp = stage[(L + 1) % TST];
+      const float4 cur = *reinterpret_cast<const float4*>(Pc + c);
+      const float4 s4 = *reinterpret_cast<const float4*>(Pc + c - TPX);
+      const float4 n4 = *reinterpret_cast<const float4*>(Pc + c + TPX);
+      const float4 b4 = *reinterpret_cast<const float4*>(Pm + c);
+      const float4 f4 = *reinterpret_cast<const float4*>(Pp + c);
+      const float w = Pc[c - 1], e = Pc[c + 4];
+      float4 r;
+      r.x = c0 * cur.x + rx * (w + cur.y) + ry * (s4.x + n4.x) + rz * (b4.x + f4.x);
+      r.y = c0 * cur.y + rx * (cur.x + cur.z) + ry * (s4.y + n4.y) + rz * (b4.y + f4.y);
+      r.z = c0 * cur.z + rx * (cur.y + cur.w) + ry * (s4.z + n4.z) + rz * (b4.z + f4.z);
+      r.w = c0 * cur.w + rx * (cur.z + e) + ry * (s4.w + n4.w) + rz * (b4.w + f4.w);
+      *reinterpret_cast<float4*>(out + zi * plane + (long long)gy * a.nx + gx) = r;
+    }
+    // every thread is done with the stage of load L-1: refill it two planes ahead
+    __syncthreads();
+    if (L - 1 + TST < nload) {
+      if (tid == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue(L - 1 + TST);
+      }
+      ++issued;
+    }
+  }
+  if (aborted && tid == 0) {
+    atomicExch(a.err, 1);
+    // wait (bounded) for this block's own loads still in flight before exiting,
+    // so that no copy lands in shared memory after the block has left
+    for (int L = waited; L < issued; ++L) mbar_wait(&bar[L % TST], (L / TST) & 1);
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+}  // namespace
+
+#ifndef PR_TMA
+#define PR_TMA 1
+#endif
+
+// Tensor maps of the two FP32 ping-pong buffers (4D: x, y, z, slice; box of
+// one staged plane); false when the path does not apply or encoding fails.
+bool tma_prepare(pr_ctx* c) {
+  c->tma_ok = false;
+  const Geom& g = c->g;
+  if (!PR_TMA || g.dim != 3 || g.nx % 4 != 0 || c->var_kappa || c->prob.f_prec != 32 ||
+      c->prob.f_scheme != PR_EXPLICIT_EULER || !c->f32a || !c->f32b)
+    return false;
+  if (g.nx > (1 << 30) || g.ny > (1 << 30) || g.nz > (1 << 30)) return false;
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+  if (!fn) return false;
+  static_assert(sizeof(CUtensorMap) == sizeof(c->tma_map[0]), "tensor map size");
+  const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz,
+                              (cuuint64_t)c->prob.N};
+  const cuuint64_t strides[3] = {(cuuint64_t)g.nx * 4, (cuuint64_t)g.nx * g.ny * 4,
+                                 (cuuint64_t)g.M * 4};
+  const cuuint32_t box[4] = {TPX, TPY, 1, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  float* bufs[2] = {c->f32a, c->f32b};
+  for (int i = 0; i < 2; ++i) {
+    CUtensorMap m;
+    if (fn(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, bufs[i], dims, strides, box, estr,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+    memcpy(c->tma_map[i], &m, sizeof m);
+  }
+  if (cudaMalloc(&c->tma_err, sizeof(int)) != cudaSuccess) return false;
+  if (cudaMemsetAsync(c->tma_err, 0, sizeof(int), c->stream) != cudaSuccess) return false;
+  c->tma_ok = true;
+  return true;
+}
+
+// One FP32 step from one ping-pong buffer to the other (src must be f32a or f32b).
+cudaError_t tma_step(pr_ctx* c, const float* src, float* dst, int count) {
+  const Geom& g = c->g;
+  const int which = src == c->f32a ? 0 : 1;
+  CUtensorMap m;
+  memcpy(&m, c->tma_map[which], sizeof m);
+  TmaArgs a{};
+  a.nx = g.nx;
+  a.ny = g.ny;
+  a.nz = g.nz;
+  a.zchunks = (g.nz + TZC - 1) / TZC;
+  a.M = g.M;
+  a.c0 = static_cast<float>(c->fst.c0);
+  a.rx = static_cast<float>(c->fst.rx);
+  a.ry = static_cast<float>(c->fst.ry);
+  a.rz = static_cast<float>(c->fst.rz);
+  a.out = dst;
+  a.err = c->tma_err;
+  dim3 grd((g.nx + TTX - 1) / TTX, (g.ny + TTY - 1) / TTY, count * a.zchunks);
+  step3d_tma<<<grd, TMA_THREADS, 0, c->stream>>>(m, a);
+  return cudaGetLastError();
+}
+
+// Error word of the TMA path (1 after a bounded wait expired); resets it.
+int tma_take_error(pr_ctx* c) {
+  if (!c->tma_err) return 0;
+  int v = 0;
+  if (cudaMemcpyAsync(&v, c->tma_err, sizeof v, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaMemsetAsync(c->tma_err, 0, sizeof v, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return 1;
+  return v;
+}
+
+}  // namespace pr
