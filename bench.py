@@ -82,8 +82,11 @@ CN_OPS_PER_LUP = {2: 13, 3: 17}
 NOMINAL_FP64_OPS = 625.0  # G FP64-pipe ops/s: 1.25 TFLOP/s nominal / 2 flops per DFMA
 # DRAM bytes (read + write) per cell update of the dominant kernel, from one ncu capture
 # of the current kernel; None where no capture of the current kernel exists.
-# (profiles/step2d_fp64_heat2d_1024x1024.md: 1016.3 MB for 63 x 1048576 updates).
-NCU_TRAFFIC_PER_LUP = {"heat2d_explicit": 1016.3e6 / (63 * 1048576)}
+# (profiles/step2d_fp64_heat2d_1024x1024.md: 1016.3 MB for 63 x 1048576 updates;
+# profiles/step3d_tma_fp32_heat3d_160cubed.md: 493.6 MB for 15 x 160^3 updates, a
+# smaller case of the same kernel whose traffic grows in proportion to the updates).
+NCU_TRAFFIC_PER_LUP = {"heat2d_explicit": 1016.3e6 / (63 * 1048576),
+                       "heat3d_mixed": 493.6e6 / (15 * 160 ** 3)}
 
 
 def parse():
