@@ -655,7 +655,9 @@ def run_ours(args, world, rank, local):
                       "parallelism": "replicas" if world > 1 else "1 GPU",
                       "schedule": ("pipelined (F of k+1 overlaps the sweep of k)"
                                    if args.pipeline else "plain"),
-                      "coarse_solver": ("CG preconditioned by %d FP32 Chebyshev steps" % args.g_cheb
+                      "coarse_solver": ("Thomas (partition tridiagonal solver)"
+                                        if p.get("g_solver") == "thomas" else
+                                        "CG preconditioned by %d FP32 Chebyshev steps" % args.g_cheb
                                         if args.g_cheb else "CG"),
                       "l2": "inputs larger than L2 (trajectory %.2f GB + workspaces)" % (
                           (N + 1) * M * 8 / 1e9)},
