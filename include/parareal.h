@@ -43,7 +43,8 @@ enum pr_status {
   PR_OK = 0,
   PR_EINVAL = 1,    /* invalid argument or problem (sizes, alignment, stability) */
   PR_ENOMEM = 2,    /* device allocation failed */
-  PR_ECUDA = 3,     /* a CUDA call failed */
+  PR_ECUDA = 3,     /* a CUDA call failed, or a bounded device wait of the trapezoidal
+                       or TMA-fed fine kernels expired (the message names it) */
   PR_ETIMEOUT = 4,  /* an asynchronous run exceeded its wall-clock limit */
   PR_ENOTCONV = 5,  /* max_iter reached before the tolerance; results written */
   PR_ESTATE = 6,    /* call out of order (e.g. run before set_problem) */
@@ -63,8 +64,12 @@ enum pr_solver { PR_SOLVER_THOMAS = 0, PR_SOLVER_CG = 1 };
  *    dim 1 by the tridiagonal partition solver (exact), dim 2/3 by conjugate
  *    gradients started from the current state and stopped when
  *    ||r||_2 <= f_rtol ||rhs||_2 or after f_maxit iterations.  FP64 only.
+ *  Explicit FP64 steps with kappa = 1 run in a scaled form (the state carried
+ *    as u / rx^j, one FP64 instruction less per point): the same values up to
+ *    rounding.
  *  f_prec: 64 = FP64 fine steps; 32 = FP32 fine steps with FP64 input and
- *    output (the coarse sweep, correction and test stay FP64).
+ *    output (the coarse sweep, correction and test stay FP64); in 3D with
+ *    kappa = 1 and n[0] % 4 == 0 the middle FP32 steps are fed by TMA.
  *  g_solver: PR_SOLVER_THOMAS (dim 1) or PR_SOLVER_CG; G = one implicit
  *    Euler step of size dT = (T-T0)/N (g_steps must be 1 with CG).
  *  g_rtol/g_maxit: CG stops when ||r||_2 <= g_rtol*||b||_2 or after g_maxit.
@@ -143,15 +148,18 @@ typedef struct pr_event {
 int parareal_create(pr_ctx** out, int device, void* cuda_stream);
 
 /* Validate and bind a problem (§3.1); allocates the workspaces it needs
- * (about 4 N M doubles for the sync path).  Rejects an unstable explicit step
- * (dt * bound(lambda_max(A)) > 2) with PR_EINVAL. */
+ * (about 4 N M doubles for the sync path, plus N M floats x 2 for FP32 fine
+ * steps and 6 M doubles per team for trapezoidal steps in 2D/3D).  Rejects an
+ * unstable explicit step (dt * bound(lambda_max(A)) > 2) with PR_EINVAL. */
 int parareal_set_problem(pr_ctx* ctx, const pr_problem* prob);
 
 /* Synchronous Parareal, Algorithm 1 (§4.1) / Eq. (11): predictor G-chain,
  * batched F over the active slices, sequential coarse sweep with the fused
  * correction lam_i = (w_new + v_i) - w_old and per-slice max-norm increment,
  * stop test Eq. (22).  lam_out_dev: (N+1)*M doubles, written with the final
- * iterate (row 0 = u0).  Returns PR_ENOTCONV if max_iter < N stopped it. */
+ * iterate (row 0 = u0).  Returns PR_ENOTCONV if max_iter < N stopped it.
+ * With trapezoidal fine steps in 2D/3D the plain schedule is used whatever
+ * PR_OPT_PIPELINE says (that F is itself a device-wide cooperative launch). */
 int parareal_run_sync(pr_ctx* ctx, double* lam_out_dev, pr_stats* stats);
 
 /* Same as parareal_run_sync with host buffers: copies u0_host (M doubles) to
@@ -165,7 +173,8 @@ int parareal_run_sync_host(pr_ctx* ctx, const double* u0_host, double* lam_out_h
  * flags and take the freshest visible predecessor version, with no global
  * barrier.  lam_out_dev receives each slice's last published version.
  * log_host (capacity log_cap events, may be NULL) receives the event log in
- * publication order; *log_len its length. */
+ * publication order; *log_len its length.  Needs the CG coarse solver and
+ * explicit fine steps (or trapezoidal steps in 2D/3D); PR_EINVAL otherwise. */
 int parareal_run_async(pr_ctx* ctx, const pr_async_opts* opts, double* lam_out_dev,
                        pr_stats* stats, pr_event* log_host, size_t log_cap, size_t* log_len);
 
