@@ -354,8 +354,9 @@ int run_adjoint_async(pr_ctx* c, const pr_event* log, size_t n_events, const dou
   }
   const int B = std::min(kmax, 16);  // events per batched fine adjoint
   const long long Mr = ring_count(g);
+  const size_t ptr_words = 3 * (2 * n_events + 16);  // device pointer triples of the batches
   const size_t words = 2 * nver * M + nw * M + (size_t)std::max(nf - 1, 1) * B * M +
-                       3 * (size_t)B * M + M + (var ? (size_t)Mr : 0);
+                       3 * (size_t)B * M + M + (var ? (size_t)Mr : 0) + ptr_words;
   const size_t bytes = words * sizeof(double);
   if (c->adj_ws_bytes < bytes) {
     if (c->adj_ws) cudaFree(c->adj_ws);
@@ -399,23 +400,69 @@ int run_adjoint_async(pr_ctx* c, const pr_event* log, size_t n_events, const dou
     return ev[i][k - 1].vG > ev[i][k - 1].vF ? W + (wbase[i] + k - 1) * M : w_before(i, k);
   };
 
+  // pointer triples (b, x0, out) of the batched coarse solves, one segment per
+  // batch, kept for the whole call (the copies to the device are asynchronous)
+  std::vector<const double*> ptrs;
+  ptrs.reserve(3 * (2 * n_events + 16));
+  const double** dptr = reinterpret_cast<const double**>(kbar ? kbar + Mr : zbuf + M);
+  size_t dpos = 0;
+  auto batch = [&](const std::vector<const double*>& bs, const std::vector<const double*>& xs,
+                   const std::vector<double*>& outs) -> cudaError_t {
+    const int n = (int)bs.size();
+    if (n == 0) return cudaSuccess;
+    const size_t at = ptrs.size();
+    for (int q = 0; q < n; ++q) ptrs.push_back(bs[q]);
+    for (int q = 0; q < n; ++q) ptrs.push_back(xs[q]);
+    for (int q = 0; q < n; ++q) ptrs.push_back(outs[q]);
+    const double** d = dptr + dpos;
+    dpos += 3 * (size_t)n;
+    cudaError_t e = cudaMemcpyAsync(d, ptrs.data() + at, 3 * n * sizeof(double*),
+                                    cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return e;
+    // the third segment holds the (mutable) output pointers
+    double* const* outs_dev = reinterpret_cast<double* const*>(const_cast<double**>(d + 2 * n));
+    return gbatch_solve(c, d, d + n, outs_dev, n);
+  };
+
   // ------------------------------------------------ forward replay
+  // Slice by slice (a version depends only on versions of the previous slice):
+  // the fine propagations of a slice's updates in batches of B, its coarse
+  // solves in one batch started from the slice's predictor value, then the
+  // corrections in version order.
   PR_CUDA(c, cudaMemcpyAsync(V(ver, 0, 0), p.u0_dev, M * sizeof(double), cudaMemcpyDeviceToDevice,
                              c->stream));
   for (int i = 1; i <= N; ++i) PR_CUDA(c, solve(V(ver, i - 1, 0), V(ver, i - 1, 0), V(ver, i, 0)));
   unsigned long long* dscratch = c->delta_dev;
   for (int i = 1; i <= N; ++i) {
-    for (int k = 1; k <= (int)ev[i].size(); ++k) {
-      const AEvent& a = ev[i][k - 1];
-      PR_CUDA(c, fine_apply(c, V(ver, i - 1, a.vF), zbuf, 1));
-      double* wo = w_before(i, k);
-      double* wn = w_after(i, k);
-      if (a.vG > a.vF) PR_CUDA(c, solve(V(ver, i - 1, a.vG), wo, wn));
-      PR_CUDA(c, cudaMemcpyAsync(V(ver, i, k), V(ver, i, k - 1), M * sizeof(double),
-                                 cudaMemcpyDeviceToDevice, c->stream));
-      PR_CUDA(c, correct(c, wn, zbuf, wo, V(ver, i, k), dscratch));
+    const int K = (int)ev[i].size();
+    {
+      std::vector<const double*> bs, xs;
+      std::vector<double*> outs;
+      for (int k = 1; k <= K; ++k) {
+        const AEvent& a = ev[i][k - 1];
+        if (a.vG == a.vF) continue;
+        bs.push_back(V(ver, i - 1, a.vG));
+        xs.push_back(V(ver, i, 0));
+        outs.push_back(W + (wbase[i] + k - 1) * M);
+      }
+      PR_CUDA(c, batch(bs, xs, outs));
+    }
+    for (int k0 = 1; k0 <= K; k0 += B) {
+      const int cnt = std::min(B, K - k0 + 1);
+      for (int q = 0; q < cnt; ++q)
+        PR_CUDA(c, cudaMemcpyAsync(xbuf + (size_t)q * M, V(ver, i - 1, ev[i][k0 + q - 1].vF),
+                                   M * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+      PR_CUDA(c, fine_apply(c, xbuf, abuf0, cnt));
+      for (int q = 0; q < cnt; ++q) {
+        const int k = k0 + q;
+        PR_CUDA(c, cudaMemcpyAsync(V(ver, i, k), V(ver, i, k - 1), M * sizeof(double),
+                                   cudaMemcpyDeviceToDevice, c->stream));
+        PR_CUDA(c, correct(c, w_after(i, k), abuf0 + (size_t)q * M, w_before(i, k), V(ver, i, k),
+                           dscratch));
+      }
     }
   }
+  if (gbatch_take_error(c)) return fail(c, PR_ECUDA, "batched coarse solve: a bounded wait expired");
   const int lastN = (int)ev[N].size();
   if (lamN)
     PR_CUDA(c, cudaMemcpyAsync(lamN, V(ver, N, lastN), M * sizeof(double), cudaMemcpyDeviceToDevice,
@@ -427,17 +474,35 @@ int run_adjoint_async(pr_ctx* c, const pr_event* log, size_t n_events, const dou
   PR_CUDA(c, axpy(V(lb, N, lastN), gN, 1.0, M));
   for (int i = N; i >= 1; --i) {
     const int K = (int)ev[i].size();
-    // coarse terms, one solve per event whose coarse input changed
-    for (int k = K; k >= 1; --k) {
-      const AEvent& a = ev[i][k - 1];
-      if (a.vG == a.vF) continue;
-      PR_CUDA(c, solve(V(lb, i, k), V(lb, i, k), zbuf));
-      PR_CUDA(c, axpy(V(lb, i - 1, a.vG), zbuf, 1.0, M));
-      PR_CUDA(c, axpy(V(lb, i - 1, a.vF), zbuf, -1.0, M));
-      if (var) {
-        facegrad_kernel<<<blocks, 256, 0, c->stream>>>(g, kbar, zbuf, w_after(i, k), 1, -c->dT);
-        facegrad_kernel<<<blocks, 256, 0, c->stream>>>(g, kbar, zbuf, w_before(i, k), 1, c->dT);
-        PR_CUDA(c, cudaGetLastError());
+    // coarse terms: the solves z = G g of the updates whose coarse input changed,
+    // in batches of B (their seeds g = lbar(i, k) are final), then the adjoint
+    // accumulations and kappa terms in version order
+    {
+      std::vector<int> ks;
+      for (int k = K; k >= 1; --k)
+        if (ev[i][k - 1].vG != ev[i][k - 1].vF) ks.push_back(k);
+      for (size_t q0 = 0; q0 < ks.size(); q0 += B) {
+        const int cnt = (int)std::min<size_t>(B, ks.size() - q0);
+        std::vector<const double*> bs, xs;
+        std::vector<double*> outs;
+        for (int q = 0; q < cnt; ++q) {
+          bs.push_back(V(lb, i, ks[q0 + q]));
+          xs.push_back(V(lb, i, ks[q0 + q]));
+          outs.push_back(states + (size_t)q * M);
+        }
+        PR_CUDA(c, batch(bs, xs, outs));
+        for (int q = 0; q < cnt; ++q) {
+          const int k = ks[q0 + q];
+          const AEvent& a = ev[i][k - 1];
+          const double* z = states + (size_t)q * M;
+          PR_CUDA(c, axpy(V(lb, i - 1, a.vG), z, 1.0, M));
+          PR_CUDA(c, axpy(V(lb, i - 1, a.vF), z, -1.0, M));
+          if (var) {
+            facegrad_kernel<<<blocks, 256, 0, c->stream>>>(g, kbar, z, w_after(i, k), 1, -c->dT);
+            facegrad_kernel<<<blocks, 256, 0, c->stream>>>(g, kbar, z, w_before(i, k), 1, c->dT);
+            PR_CUDA(c, cudaGetLastError());
+          }
+        }
       }
     }
     // fine terms, batched over up to B events: gather inputs and adjoint seeds

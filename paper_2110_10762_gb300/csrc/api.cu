@@ -63,6 +63,7 @@ void free_problem(pr_ctx* c) {
   tri_free(&c->tri_g);
   cn_free(c);
   cheb_free(c);
+  gbatch_free(c);
   pipeline_free(c);
   c->fvar = {};
   c->gvar = {};

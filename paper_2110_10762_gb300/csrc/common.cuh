@@ -121,6 +121,12 @@ struct pr_ctx {
   int* cn_err = nullptr;
   unsigned long long* cn_iters = nullptr;
   int cn_teams = 0, cn_cap = 0;
+  // batched coarse solves (gbatch.cu): team workspaces and control words
+  double* gb_work = nullptr;
+  double* gb_part = nullptr;
+  unsigned long long* gb_bar = nullptr;
+  int* gb_err = nullptr;
+  int gb_teams = 0, gb_cap = 0;
   // async / adjoint workspaces are allocated lazily by their drivers
   void* async_ws = nullptr;
   size_t async_ws_bytes = 0;
@@ -152,6 +158,14 @@ int scaled_period(double rx);
 // One FP64 explicit step u' = S u on `count` states (S is symmetric, so this is
 // also the transposed step used by the adjoint).
 cudaError_t explicit_step64(pr_ctx* c, const double* in, double* out, int count);
+
+// ---- batched coarse solves over independent systems (gbatch.cu)
+// (I + dT A) out[j] = b[j] from x0[j], j < count (device arrays of pointers;
+// out[j] aliases neither b[j] nor x0[j]).  Asynchronous on the context stream.
+cudaError_t gbatch_solve(pr_ctx* c, const double* const* b_dev, const double* const* x0_dev,
+                         double* const* out_dev, int count);
+int gbatch_take_error(pr_ctx* c);
+void gbatch_free(pr_ctx* c);
 
 // ---- trapezoidal-rule fine propagator in 2D/3D (cn.cu)
 cudaError_t cn_alloc(pr_ctx* c);
