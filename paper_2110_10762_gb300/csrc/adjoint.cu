@@ -352,7 +352,13 @@ int run_adjoint_async(pr_ctx* c, const pr_event* log, size_t n_events, const dou
     nw += ev[i].size();
     kmax = std::max(kmax, (int)ev[i].size());
   }
-  const int B = std::min(kmax, 16);  // events per batched fine adjoint
+  // events per batch of fine propagations / fine adjoints: all of a slice's
+  // updates when the recomputed states fit in about 16 GB, at most 64
+  const double per_event = (double)std::max(nf, 2) * M * sizeof(double);
+  const int b_mem = std::max(1, (int)(16e9 / per_event));
+  // (and at most N: the batched fine propagation ping-pongs through the N-state
+  // workspace of the context)
+  const int B = std::min(std::min(std::min(kmax, 64), b_mem), N);
   const long long Mr = ring_count(g);
   const size_t ptr_words = 3 * (2 * n_events + 16);  // device pointer triples of the batches
   const size_t words = 2 * nver * M + nw * M + (size_t)std::max(nf - 1, 1) * B * M +

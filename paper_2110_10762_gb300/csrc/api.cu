@@ -119,6 +119,8 @@ cudaError_t fine_batch(pr_ctx* c, const double* in, double* out, int count) {
 // F on `count` consecutive states: explicit steps, or implicit / trapezoidal
 // steps by the tridiagonal solver (1D) or the batched CG kernel (2D/3D).
 cudaError_t fine_apply(pr_ctx* c, const double* in, double* out, int count) {
+  // the explicit and FP32 paths ping-pong through N-state workspaces
+  if (count < 0 || count > c->prob.N) return cudaErrorInvalidValue;
   if (c->prob.f_scheme == PR_EXPLICIT_EULER)
     return explicit_fine(c, in, out, count, c->prob.f_steps, c->prob.f_prec);
   if (c->prob.f_scheme == PR_CRANK_NICOLSON && c->g.dim > 1) return cn_fine(c, in, out, count);

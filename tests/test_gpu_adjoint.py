@@ -212,6 +212,24 @@ def test_async_adjoint_matches_oracle_random_log(name, seed):
         assert rel_l2(gk, ref_k) < ADJ_TOL
 
 
+def test_async_adjoint_with_more_updates_per_slice_than_slices():
+    """A log in which every slice publishes many more versions than there are slices:
+    the batched fine propagations and adjoints of one slice's updates are split into
+    batches of at most N states (the context's workspaces hold N)."""
+    from oracle.adjoint import adjoint_async
+    p = small("heat2d_inverse")
+    p["N"] = 3
+    events = random_log(p["N"], 46, max_events=40)
+    per_slice = max(sum(1 for e in events if e[0] == i) for i in range(1, 4))
+    assert per_slice > p["N"]
+    g = np.random.default_rng(47).standard_normal(tuple(reversed(p["n"])))
+    ref_u0, ref_k, ref_lam = adjoint_async(p, events, g)
+    gu0, gk, lamN = gpu_adjoint_async(p, events, g)
+    assert rel_l2(lamN, ref_lam) < 1e-12
+    assert rel_l2(gu0, ref_u0) < ADJ_TOL
+    assert rel_l2(gk, ref_k) < ADJ_TOL
+
+
 def test_async_adjoint_of_sync_schedule_equals_sync_adjoint():
     """The synchronous schedule written as a log: both GPU adjoints agree."""
     p = small("heat2d_inverse")
