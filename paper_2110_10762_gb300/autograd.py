@@ -7,7 +7,9 @@ lambda_N with respect to the initial state u0 and the node diffusivity kappa
 come from the hand-written reverse sweep in libparareal (no autograd tape).
 
 spec: dict with dim, n (x, y, z sizes), T (end time, T0 = 0), N (slices),
-f_steps, K (iterations), g_rtol (coarse CG tolerance; default 1e-13).
+f_steps, K (iterations), g_rtol (coarse CG tolerance; default 1e-13), and
+optionally f_scheme ("explicit", default, or "implicit" for 1D implicit fine
+steps) and g_solver ("cg", default, or "thomas" in 1D).
 """
 from __future__ import annotations
 
@@ -17,9 +19,13 @@ from . import api
 
 
 def _problem(spec, u0, kappa, K):
+    from ._abi import PR_EXPLICIT_EULER, PR_IMPLICIT_EULER, PR_SOLVER_CG, PR_SOLVER_THOMAS
+    f_scheme = PR_IMPLICIT_EULER if spec.get("f_scheme") == "implicit" else PR_EXPLICIT_EULER
+    g_solver = PR_SOLVER_THOMAS if spec.get("g_solver") == "thomas" else PR_SOLVER_CG
     return api.make_problem(dim=spec["dim"], n=spec["n"], T0=0.0, T=spec["T"], N=spec["N"],
-                            u0=u0, kappa=kappa, f_steps=spec["f_steps"], f_prec=64,
-                            g_rtol=spec.get("g_rtol", 1e-13), tol=0.0, max_iter=K)
+                            u0=u0, kappa=kappa, f_scheme=f_scheme, f_steps=spec["f_steps"],
+                            f_prec=64, g_solver=g_solver, g_rtol=spec.get("g_rtol", 1e-13),
+                            tol=0.0, max_iter=K)
 
 
 class ParaRealFn(torch.autograd.Function):

@@ -125,6 +125,25 @@ def test_autograd_function_matches_adjoint():
     assert rel_l2(host(kap.grad), ref_k) < ADJ_TOL
 
 
+def test_autograd_function_1d_implicit_thomas():
+    """ParaRealFn with 1D implicit fine steps and the Thomas coarse step."""
+    from paper_2110_10762_gb300.autograd import ParaRealFn
+    p = preset("heat1d_thomas", "small")
+    rng = np.random.default_rng(72)
+    p["kappa"] = np.exp(0.3 * rng.standard_normal(p["n"][0] + 2))
+    K = 2
+    spec = dict(dim=1, n=p["n"], T=p["N"] * p["f_steps"] * p["dt"], N=p["N"],
+                f_steps=p["f_steps"], K=K, f_scheme="implicit", g_solver="thomas")
+    u0 = dev(p["u0"]).requires_grad_(True)
+    kap = dev(p["kappa"]).requires_grad_(True)
+    out = ParaRealFn.apply(u0, kap, spec)
+    (0.5 * (out ** 2).sum()).backward()
+    ref_u0, ref_k, lamN = adjoint_sync(dict(p, tol=0.0), host(out), K)
+    assert rel_l2(host(out), lamN) < 1e-12
+    assert rel_l2(host(u0.grad), ref_u0) < 1e-12
+    assert rel_l2(host(kap.grad), ref_k) < 1e-11
+
+
 def test_adjoint_rejects_unsupported():
     p = small(f_prec=32)
     with Ctx(p) as c:
