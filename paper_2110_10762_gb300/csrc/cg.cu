@@ -344,6 +344,10 @@ __global__ void copy_kernel(double* __restrict__ d, const double* __restrict__ s
 }
 
 constexpr long long CG_L2_POINTS = 2LL << 20;  // 5 FP64 vectors of 2 M points = 80 MB
+#ifndef PR_CG_BIG_MINB
+#define PR_CG_BIG_MINB 4
+#endif
+constexpr int CG_BIG = PR_CG_BIG_MINB;  // blocks per SM of the instance for grids beyond L2
 
 template <int MINB, bool PCG = false>
 int cg_blocks_of(int num_sms) {
@@ -359,8 +363,8 @@ int cg_blocks_of(int num_sms) {
 }  // namespace
 
 int cg_max_blocks(int num_sms) {
-  const int a = std::max(cg_blocks_of<2>(num_sms), cg_blocks_of<4>(num_sms));
-  const int b = std::max(cg_blocks_of<2, true>(num_sms), cg_blocks_of<4, true>(num_sms));
+  const int a = std::max(cg_blocks_of<2>(num_sms), cg_blocks_of<CG_BIG>(num_sms));
+  const int b = std::max(cg_blocks_of<2, true>(num_sms), cg_blocks_of<CG_BIG, true>(num_sms));
   return a > b ? a : b;
 }
 
@@ -410,7 +414,7 @@ cudaError_t cg_solve(pr_ctx* c, const CgArgs& in) {
   }
   const bool big = c->g.M > CG_L2_POINTS;
   const bool pcg = a.ch.m >= 2;
-  int cap = big ? (pcg ? cg_blocks_of<4, true>(c->num_sms) : cg_blocks_of<4>(c->num_sms))
+  int cap = big ? (pcg ? cg_blocks_of<CG_BIG, true>(c->num_sms) : cg_blocks_of<CG_BIG>(c->num_sms))
                 : (pcg ? cg_blocks_of<2, true>(c->num_sms) : cg_blocks_of<2>(c->num_sms));
   // a caller-chosen blocks-per-SM cap leaves room for concurrent kernels
   if (c->opt_cg_bps > 0 && c->opt_cg_bps * c->num_sms < cap) cap = c->opt_cg_bps * c->num_sms;
@@ -419,7 +423,7 @@ cudaError_t cg_solve(pr_ctx* c, const CgArgs& in) {
   if (blocks > c->cg_blocks) blocks = c->cg_blocks;  // partials are sized for cg_blocks
   if (blocks < 1) blocks = 1;
   void* args[] = {&a};
-  void* fn = big ? (pcg ? (void*)cg_kernel<4, true> : (void*)cg_kernel<4, false>)
+  void* fn = big ? (pcg ? (void*)cg_kernel<CG_BIG, true> : (void*)cg_kernel<CG_BIG, false>)
                  : (pcg ? (void*)cg_kernel<2, true> : (void*)cg_kernel<2, false>);
   return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(CG_THREADS), args, 0, c->stream);
 }
