@@ -1,0 +1,28 @@
+"""Host-side pieces of bench.py that need no GPU: the §4.1 cost model."""
+import types
+
+import bench
+
+
+def test_cost_model_recovers_the_overhead_of_eq_pr_cost():
+    """Build a solve time from Eq. (pr_cost) with a constant overhead C_bar per
+    processor and iteration (its double sum written out), and recover C_bar."""
+    p, k, C_F, C_G, C_bar = 8, 3, 10.0, 1.0, 0.5
+    overhead = sum(C_bar for l in range(1, k + 1) for j in range(l + 1, p))
+    T = p * C_G + k * (C_F + C_G) + overhead
+    st = {"iterations": k, "coarse_solves": 20, "t_fine_ms": k * C_F, "t_coarse_ms": 20 * C_G}
+    cm = bench.cost_model_sync({"N": p}, st, T)
+    assert abs(cm["C_F_ms"] - C_F) < 1e-12 and abs(cm["C_G_ms"] - C_G) < 1e-12
+    assert abs(cm["aubanel_ms"] - (p * C_G + k * (C_F + C_G))) < 1e-12
+    assert abs(cm["C_bar_ms"] - C_bar) < 1e-12
+
+
+def test_async_cost_model_reads_the_log():
+    ev = lambda i, k, vF, vG, t0, t1: types.SimpleNamespace(slice=i, version=k, vF=vF, vG=vG,
+                                                          t_start=t0, t_end=t1)
+    log = [ev(1, 1, 0, 0, 0, 4_000_000), ev(2, 1, 0, 1, 0, 5_000_000),
+           ev(2, 2, 1, 1, 5_000_000, 9_000_000)]
+    cm = bench.cost_model_async(log, 2, 9.0)
+    assert cm["kappa"] == 2 and cm["updates"] == 3
+    assert cm["update_F_ms"] == 4.0 and cm["update_FG_ms"] == 5.0
+    assert cm["n_F_only"] == 2 and cm["n_FG"] == 1
