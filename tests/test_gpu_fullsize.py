@@ -78,3 +78,62 @@ def test_heat3d_varkappa_fp32_fine_step_full_size():
         got = host(out).reshape(x0.shape)
     err = rel_l2(got, P.F(x0))
     assert 1e-12 < err < 1e-5, err
+
+
+def test_heat1d_thomas_workload_full_size():
+    """1023 points, N = 16, F = 100 implicit-Euler steps, G by Thomas, tol 1e-10.
+    The oracle runs the first three iterations at full size: the stacked
+    (N+1) x M trajectory of every iterate k = 1..3 must match
+    within 1e-12 relative L2; the converged run must stop with its last
+    increment below tol and sit on the oracle's serial fine solution."""
+    from oracle.parareal import serial_fine, sync_parareal
+
+    p = preset("heat1d_thomas", "full")
+    K = 3
+    ref = sync_parareal(p, tol=0.0, max_iter=K, record=True)
+    for k in range(1, K + 1):
+        with Ctx(p, tol=0.0, max_iter=k) as c:
+            lam = c.lam()
+            code, st = pr.parareal_run_sync(c.ctx, lam)
+            got = host(lam).reshape(p["N"] + 1, -1)
+        assert st.iterations == k
+        assert rel_l2(got, ref.iterates[k]) < 1e-12, k
+    with Ctx(p) as c:
+        lam = c.lam()
+        code, st = pr.parareal_run_sync(c.ctx, lam)
+        got = host(lam).reshape(p["N"] + 1, -1)
+    assert code == pr.PR_OK and st.converged and st.max_delta < p["tol"]
+    star = serial_fine(p)
+    assert np.max(np.abs(got - star)) < 100 * p["tol"] * max(1.0, np.max(np.abs(star)))
+    assert np.array_equal(got[0], p["u0"].reshape(-1))
+
+
+def test_heat2d_async_workload_full_size():
+    """The asynchronous kernel on the 1024^2, N = 64 FP64 workload in the launch
+    configuration the benchmark times (automatic teams, no delays, tol 1e-10).
+    Checked: the log is a valid asynchronous schedule (consecutive versions,
+    fine input = previous coarse input, a coarse solve exactly when the input
+    changed); slice 1 is exactly F(u0) by the oracle; and sampled slices sit
+    on the fine propagation of their predecessor, lambda_i = F(lambda_{i-1}),
+    within the order of the stop tolerance."""
+    p = preset("heat2d_explicit", "full")
+    P = heat.Propagators(p)
+    shape = tuple(reversed(p["n"]))
+    with Ctx(p) as c:
+        lam = c.lam()
+        opts = pr.make_async_opts(timeout_s=120.0)
+        code, st, log = pr.parareal_run_async(c.ctx, opts, lam, log_cap=1 << 20)
+        L = host(lam).reshape((p["N"] + 1,) + shape)
+    assert code == pr.PR_OK and st.converged and st.iterations >= 1
+    last = {i: (0, 0) for i in range(1, p["N"] + 1)}
+    for e in sorted(log, key=lambda e: (e.slice, e.version)):
+        k, vG = last[e.slice]
+        assert e.version == k + 1 and e.vF == vG and e.vG >= e.vF
+        assert e.cg_iters == 0 or e.vG > e.vF   # no solve when the input did not change
+        last[e.slice] = (e.version, e.vG)
+    assert all(v >= 1 for v, _ in last.values())
+    assert np.array_equal(L[0], p["u0"])
+    assert rel_l2(L[1], P.F(p["u0"])) < 1e-12
+    for i in (2, p["N"] // 2, p["N"]):
+        gap = np.max(np.abs(L[i] - P.F(L[i - 1])))
+        assert gap < 20 * p["tol"], (i, gap)

@@ -526,3 +526,26 @@ def test_coarse_solves_follow_algorithm_1():
                 assert cg[i - 1] > 0, (k, i)
             else:
                 assert cg[i - 1] == 0, (k, i)
+
+
+def test_tridiagonal_propagators_at_1023_points_match_closed_form():
+    """The 1D workload (1023 points, u0 = 8 sine modes): 100 implicit-Euler fine
+    steps at r = 65.536, one coarse step at r = 6553.6 and 100 trapezoidal
+    steps are exact per mode, (1 + dt mu)^-s and ((1 - dt mu/2)/(1 + dt mu/2))^s.
+    The oracle must meet them to a few ulps per solve (relative L2 <= 2e-14),
+    well inside the 1e-12 the GPU is held to."""
+    p = preset("heat1d_thomas", "full")
+    n, h = p["n"][0], p["h"][0]
+    x = np.arange(1, n + 1) * h
+    modes = np.array([np.sin(j * np.pi * x) for j in range(1, 9)])
+    coef = np.linalg.lstsq(modes.T, p["u0"].reshape(-1), rcond=None)[0]
+    mu = mode_eigs(n, h)[:8]
+    dt, dT = p["dt"], p["dt"] * p["f_steps"]
+    cases = [(heat.implicit_euler_1d(p["u0"], dt, (h,), None, p["f_steps"]),
+              (1 + dt * mu) ** (-p["f_steps"])),
+             (heat.implicit_euler_1d(p["u0"], dT, (h,), None, 1), 1 / (1 + dT * mu)),
+             (heat.crank_nicolson_1d(p["u0"], dt, (h,), None, p["f_steps"]),
+              ((1 - 0.5 * dt * mu) / (1 + 0.5 * dt * mu)) ** p["f_steps"])]
+    for got, fac in cases:
+        exact = (coef * fac) @ modes
+        assert np.linalg.norm(got - exact) / np.linalg.norm(exact) < 2e-14
