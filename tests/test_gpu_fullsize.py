@@ -137,3 +137,44 @@ def test_heat2d_async_workload_full_size():
     for i in (2, p["N"] // 2, p["N"]):
         gap = np.max(np.abs(L[i] - P.F(L[i - 1])))
         assert gap < 20 * p["tol"], (i, gap)
+
+
+def test_heat3d_varkappa_async_workload_full_size():
+    """192^3 variable kappa, N = 256, F = 32 FP32 steps, FP64 coarse CG, seeded
+    publication delays of 0-4 units, tol 1e-5: the asynchronous kernel in the
+    benchmark's launch configuration (automatic teams; the unit here is 36.6 us,
+    the measured duration of one fine step of one slice).  Checked: a valid
+    asynchronous log whose delays were honoured, slice 1 against the FP64
+    oracle's F(u0) within the mixed-precision bound, and the last slice on the
+    FP64 fine propagation of its predecessor within the stop rule's tolerance
+    plus the FP32 rounding of F."""
+    from synthetic import delay_table
+
+    p = preset("heat3d_varkappa_async", "full")
+    P64 = heat.Propagators(dict(p, f_prec=64))
+    shape = tuple(reversed(p["n"]))
+    unit_ns = 36600.0
+    table = delay_table(p["N"], 64, seed=p["delay_seed"])
+    with Ctx(p) as c:
+        delays = torch().from_numpy(table).cuda()
+        opts = pr.make_async_opts(timeout_s=240.0, delays=delays, delay_unit_ns=unit_ns)
+        lam = c.lam()
+        code, st, log = pr.parareal_run_async(c.ctx, opts, lam, log_cap=1 << 20)
+        torch().cuda.synchronize()
+        picks = (1, p["N"])
+        L = {i: host(lam[i * c.M:(i + 1) * c.M]).reshape(shape) for i in picks}
+        L.update({i - 1: host(lam[(i - 1) * c.M:i * c.M]).reshape(shape) for i in picks})
+    assert code == pr.PR_OK and st.converged
+    last = {i: (0, 0) for i in range(1, p["N"] + 1)}
+    for e in sorted(log, key=lambda e: (e.slice, e.version)):
+        k, vG = last[e.slice]
+        assert e.version == k + 1 and e.vF == vG and e.vG >= e.vF
+        # visibility = publication + delay: the update spans at least its delay
+        assert e.t_end >= e.t_start + int(table[e.slice - 1, k % 64] * unit_ns) - 1
+        last[e.slice] = (e.version, e.vG)
+    assert all(v >= 1 for v, _ in last.values())
+    ref1 = P64.F(p["u0"])
+    assert rel_l2(L[1], ref1) < 1e-5
+    scale = np.max(np.abs(ref1))
+    gap = np.max(np.abs(L[p["N"]] - P64.F(L[p["N"] - 1])))
+    assert gap < 2 * p["tol"] + 1e-5 * scale, gap
