@@ -202,6 +202,11 @@ __device__ bool team_fine_cn(const AsyncDev& a, const TeamBarrier& bar, const do
   return true;
 }
 
+#ifndef PR_ASYNC_TILE2D
+#define PR_ASYNC_TILE2D 1
+#endif
+constexpr int TEAM_RY = 4;  // rows per 2D tile of the team's fine steps
+
 // FP64 constant-kappa fine propagation in the scaled form (as the batched
 // kernel): the team carries v = u / sigma with sigma multiplied by rx every
 // step, v' = (c0/rx) v + (w + e) + (ry/rx)(s + n) + (rz/rx)(b + f), and returns
@@ -219,6 +224,38 @@ __device__ bool team_fine_scaled(const AsyncDev& a, const TeamBarrier& bar, cons
     const bool back = s == S - 1 || since == R;
     const double sig = s == S - 1 ? a.f_sigma_last : a.f_sigma_R;
     const long long plane = (long long)g.nx * g.ny;
+#if PR_ASYNC_TILE2D
+    if (g.dim == 2) {
+      // 2D: each warp walks tiles of 32 columns x TEAM_RY rows, carrying the
+      // vertical neighbours in registers (three loads per update instead of five)
+      const int nx = g.nx, ny = g.ny;
+      const int tiles_x = (nx + 31) / 32;
+      const int ntiles = tiles_x * ((ny + TEAM_RY - 1) / TEAM_RY);
+      const int wpb = blockDim.x / 32, lane = threadIdx.x % 32;
+      for (int t = tb * wpb + threadIdx.x / 32; t < ntiles; t += a.C * wpb) {
+        const int ty = t / tiles_x;
+        const int x = (t - ty * tiles_x) * 32 + lane;
+        const int y0 = ty * TEAM_RY;
+        if (x >= nx) continue;
+        double sv = y0 > 0 ? src[(long long)(y0 - 1) * nx + x] : 0.0;
+        double cur = src[(long long)y0 * nx + x];
+#pragma unroll
+        for (int j = 0; j < TEAM_RY; ++j) {
+          const int y = y0 + j;
+          if (y >= ny) break;
+          const long long i = (long long)y * nx + x;
+          const double nv = y + 1 < ny ? src[i + nx] : 0.0;
+          const double w = x > 0 ? src[i - 1] : 0.0;
+          const double e = x + 1 < nx ? src[i + 1] : 0.0;
+          double res = fma(ca, cur, w + e);
+          res = fma(cb, sv + nv, res);
+          dst[i] = back ? res * sig : res;
+          sv = cur;
+          cur = nv;
+        }
+      }
+    } else
+#endif
     for_each_point(g, tb, a.C, [&](int x, int y, int z, long long i) {
       const double w = x > 0 ? src[i - 1] : 0.0;
       const double e = x + 1 < g.nx ? src[i + 1] : 0.0;
