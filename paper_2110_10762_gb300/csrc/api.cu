@@ -420,8 +420,12 @@ int parareal_set_option(pr_ctx* c, int option, double value) {
       c->opt_g_cheb = (int)value;
       if (c->opt_g_cheb && c->has_problem) {
         cudaSetDevice(c->device);
-        PR_CUDA(c, cheb_alloc(c));
-        PR_CUDA(c, cudaStreamSynchronize(c->stream));
+        cudaError_t e = cheb_alloc(c);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) {
+          c->opt_g_cheb = 0;  // keep the plain solver usable
+          return cuda_fail(c, e, "Chebyshev workspaces");
+        }
       }
       return PR_OK;
     default:

@@ -533,6 +533,7 @@ cudaError_t cheb_alloc(pr_ctx* c) {
       c->gvar32 = {q0, qx, nfy ? qy : nullptr, nfz ? qz : nullptr};
     }
   }
+  if (e != cudaSuccess) cheb_free(c);  // the solver uses the option only when cheb_z is set
   return e;
 }
 

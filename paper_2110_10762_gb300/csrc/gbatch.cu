@@ -70,15 +70,19 @@ cudaError_t gbatch_solve(pr_ctx* c, const double* const* b_dev, const double* co
     if (t < 1) t = 1;
     if (t > c->gb_cap) t = c->gb_cap;
     c->gb_teams = t;
-    if ((e = cudaMalloc(&c->gb_work, (size_t)t * 3 * c->g.M * sizeof(double))) != cudaSuccess)
+    e = cudaMalloc(&c->gb_work, (size_t)t * 3 * c->g.M * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&c->gb_part, (size_t)c->gb_cap * 6 * sizeof(double));
+    if (e == cudaSuccess)
+      e = cudaMalloc(&c->gb_bar, (size_t)c->gb_cap * sizeof(unsigned long long) + 64);
+    if (e == cudaSuccess) {
+      c->gb_err = reinterpret_cast<int*>(c->gb_bar + c->gb_cap);
+      e = cudaMemsetAsync(c->gb_err, 0, sizeof(int), c->stream);
+    }
+    if (e != cudaSuccess) {
+      // leave no half-built workspace behind: the next call starts over
+      gbatch_free(c);
       return e;
-    if ((e = cudaMalloc(&c->gb_part, (size_t)c->gb_cap * 6 * sizeof(double))) != cudaSuccess)
-      return e;
-    if ((e = cudaMalloc(&c->gb_bar, (size_t)c->gb_cap * sizeof(unsigned long long) + 64)) !=
-        cudaSuccess)
-      return e;
-    c->gb_err = reinterpret_cast<int*>(c->gb_bar + c->gb_cap);
-    if ((e = cudaMemsetAsync(c->gb_err, 0, sizeof(int), c->stream)) != cudaSuccess) return e;
+    }
   }
   const int T = count < c->gb_teams ? count : c->gb_teams;
   const int C = c->gb_cap / T;
