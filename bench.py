@@ -113,6 +113,17 @@ def cost_model_sync(p, st, ms_per_solve):
             "serial_fine_model_ms": N * C_F}
 
 
+def sync_delay_ms(table, unit_ns, k, N):
+    """Time the injected publication delays add to a synchronous run of k
+    iterations: version j+1 of slice i is published with delay
+    table[i-1, j % cols] units, and in the synchronous sweep every published
+    correction sits on the critical path (the next slice's coarse solve
+    waits for it), so the delays of the updated slices add up."""
+    cols = table.shape[1]
+    units = sum(float(table[i - 1, j % cols]) for j in range(k) for i in range(j + 1, N + 1))
+    return units * unit_ns / 1e6
+
+
 def cost_model_async(log, N, t_ms):
     """Per-update costs of an asynchronous run read from its event log (§4.1,
     Proposition 3 charges kappa (C_F + C_G) per processor): the mean duration
@@ -458,6 +469,9 @@ def run_async_workload(args, local):
                     "fine_cg_iterations": sst.fine_cg_iterations,
                     "err_vs_serial_fine": (lam - star).abs().max().item() / scale},
            "async_speedup_vs_sync": t_sync / t_async,
+           "sync_with_same_delays_ms": (t_sync + sync_delay_ms(delay_table(N, 64, seed=p["delay_seed"]),
+                                                               unit_ns, sst.iterations, N)
+                                        if delays is not None else None),
            "cost_model": {"async": cost_model_async(log, N, t_async),
                           "sync": cost_model_sync(p, sst.as_dict(), t_sync)},
            "kappa_over_k": st.iterations / max(sst.iterations, 1),

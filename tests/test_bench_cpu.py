@@ -26,3 +26,11 @@ def test_async_cost_model_reads_the_log():
     assert cm["kappa"] == 2 and cm["updates"] == 3
     assert cm["update_F_ms"] == 4.0 and cm["update_FG_ms"] == 5.0
     assert cm["n_F_only"] == 2 and cm["n_FG"] == 1
+
+
+def test_sync_delay_sums_the_updated_slices():
+    import numpy as np
+    table = np.arange(12).reshape(3, 4)       # slices 1..3, 4 columns
+    # k = 2: iteration 0 updates slices 1..3 (column 0), iteration 1 slices 2..3 (column 1)
+    units = (0 + 4 + 8) + (5 + 9)
+    assert abs(bench.sync_delay_ms(table, 1e6, 2, 3) - units) < 1e-12
