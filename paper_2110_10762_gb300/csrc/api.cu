@@ -28,6 +28,9 @@ int fail(pr_ctx* c, int code, const std::string& msg) {
 int cuda_fail(pr_ctx* c, cudaError_t e, const char* where) {
   char buf[512];
   snprintf(buf, sizeof buf, "%s: %s", where, cudaGetErrorString(e));
+  // a failed allocation (or launch configuration) leaves a non-sticky "last
+  // error" behind; clear it so the next call's launch checks do not report it
+  cudaGetLastError();
   return fail(c, e == cudaErrorMemoryAllocation ? PR_ENOMEM : PR_ECUDA, buf);
 }
 
@@ -243,20 +246,24 @@ int parareal_set_problem(pr_ctx* c, const pr_problem* pin) {
   auto chk = [&](cudaError_t x) {
     if (e == cudaSuccess) e = x;
   };
-  chk(dalloc(&c->v, NM));
-  chk(dalloc(&c->w, NM));
-  if (p.f_scheme == PR_EXPLICIT_EULER && p.f_prec == 64) chk(dalloc(&c->tmp, NM));
+  // stop at the first failed allocation (the rest would only be freed again)
+  auto alloc = [&](auto** ptr, size_t count) {
+    if (e == cudaSuccess) e = dalloc(ptr, count);
+  };
+  alloc(&c->v, NM);
+  alloc(&c->w, NM);
+  if (p.f_scheme == PR_EXPLICIT_EULER && p.f_prec == 64) alloc(&c->tmp, NM);
   if (p.f_prec == 32) {
-    chk(dalloc(&c->f32a, NM));
-    chk(dalloc(&c->f32b, NM));
+    alloc(&c->f32a, NM);
+    alloc(&c->f32b, NM);
   }
-  chk(dalloc(&c->cg_x, g.M));
-  chk(dalloc(&c->cg_r, g.M));
-  chk(dalloc(&c->cg_p, g.M));
-  chk(dalloc(&c->cg_q, g.M));
-  chk(dalloc(&c->cg_part, 6 * (size_t)c->cg_blocks));
-  chk(dalloc(&c->cg_iters_dev, (size_t)p.N + 1));
-  chk(dalloc(&c->delta_dev, (size_t)p.N));
+  alloc(&c->cg_x, g.M);
+  alloc(&c->cg_r, g.M);
+  alloc(&c->cg_p, g.M);
+  alloc(&c->cg_q, g.M);
+  alloc(&c->cg_part, 6 * (size_t)c->cg_blocks);
+  alloc(&c->cg_iters_dev, (size_t)p.N + 1);
+  alloc(&c->delta_dev, (size_t)p.N);
   if (e != cudaSuccess) {
     free_problem(c);
     return cuda_fail(c, e, "workspace allocation");

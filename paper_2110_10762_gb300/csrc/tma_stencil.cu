@@ -214,8 +214,14 @@ bool tma_prepare(pr_ctx* c) {
       return false;
     memcpy(c->tma_map[i], &m, sizeof m);
   }
-  if (cudaMalloc(&c->tma_err, sizeof(int)) != cudaSuccess) return false;
-  if (cudaMemsetAsync(c->tma_err, 0, sizeof(int), c->stream) != cudaSuccess) return false;
+  if (cudaMalloc(&c->tma_err, sizeof(int)) != cudaSuccess ||
+      cudaMemsetAsync(c->tma_err, 0, sizeof(int), c->stream) != cudaSuccess) {
+    // optional path: fall back to the vector kernel, leaving no error behind
+    if (c->tma_err) cudaFree(c->tma_err);
+    c->tma_err = nullptr;
+    cudaGetLastError();
+    return false;
+  }
   c->tma_ok = true;
   return true;
 }

@@ -332,6 +332,31 @@ def test_invalid_problems_are_rejected():
         pr.parareal_destroy(ctx)
 
 
+def test_out_of_memory_problem_leaves_context_usable():
+    """A problem whose trajectory cannot be allocated (65536^2 x 64 slices, about
+    2 TB per array) fails with PR_ENOMEM before anything runs; the context then
+    takes an ordinary problem and solves it as usual."""
+    p = CASES["2d_const"]()
+    t = torch()
+    ctx = pr.parareal_create(0, t.cuda.current_stream())
+    try:
+        u0 = dev(p["u0"])
+        huge = pr.make_problem(dim=2, n=(65536, 65536), T0=0.0, T=1e-6, N=64, u0=u0,
+                               f_steps=16, g_rtol=1e-10, tol=1e-9)
+        with pytest.raises(pr.PararealError) as e:
+            pr.parareal_set_problem(ctx, huge)
+        assert e.value.code == pr.PR_ENOMEM
+        from .gpu_util import problem_struct
+        pr.parareal_set_problem(ctx, problem_struct(p, u0, None))
+        lam = t.zeros((p["N"] + 1) * u0.numel(), dtype=t.float64, device="cuda")
+        code, st = pr.parareal_run_sync(ctx, lam)
+        ref = sync_parareal(p)
+        assert code == pr.PR_OK and st.iterations == ref.k
+        assert rel_l2(host(lam), ref.lam) < FP64_TOL
+    finally:
+        pr.parareal_destroy(ctx)
+
+
 @pytest.mark.parametrize("case,chunks,bps", [("2d_const", 8, 0), ("2d_var", 3, 1),
                                              ("3d_var", 1, 0), ("1d_thomas", 4, 0),
                                              ("3d_const", 100, 2)])
