@@ -742,15 +742,18 @@ def run_ours(args, world, rank, local):
         outh = torch.empty((N + 1) * M, dtype=torch.float64).pin_memory()
         pr.parareal_run_sync_host(ctx, u0h, outh)
         barrier()
-        t0 = time.perf_counter()
-        e_lups = 0
-        for _ in range(args.steps):
-            _, st = pr.parareal_run_sync_host(ctx, u0h, outh)
-            e_lups += st.fine_lups
-        torch.cuda.synchronize()
-        e_value, _ = replica_aggregate(e_lups, time.perf_counter() - t0, world, "cuda")
+        with Clocks(local) as clk_e:
+            t0 = time.perf_counter()
+            e_lups = 0
+            for _ in range(args.steps):
+                _, st = pr.parareal_run_sync_host(ctx, u0h, outh)
+                e_lups += st.fine_lups
+            torch.cuda.synchronize()
+            e_sec = time.perf_counter() - t0
+        e_value, _ = replica_aggregate(e_lups, e_sec, world, "cuda")
         out["e2e"] = {"value": e_value / 1e9, "unit": "GLUP/s",
-                      "h2d_bytes_per_step": M * 8, "d2h_bytes_per_step": (N + 1) * M * 8}
+                      "h2d_bytes_per_step": M * 8, "d2h_bytes_per_step": (N + 1) * M * 8,
+                      "ms_per_step": e_sec * 1e3 / args.steps, "clocks": clk_e.summary()}
     out["clocks"] = clk.summary()
     pr.parareal_destroy(ctx)
     if rank == 0 and not args.no_cpu:
