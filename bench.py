@@ -166,6 +166,8 @@ def parse():
                     help="async workloads: CTAs per slice team (0 = automatic)")
     ap.add_argument("--lazy", action="store_true",
                     help="async workloads: skip re-updates that a newer input will supersede")
+    ap.add_argument("--verify", action="store_true",
+                    help="async workloads: confirm the stop by the fixed-point residual")
     ap.add_argument("--cg-bps", type=int, default=0,
                     help="CG blocks per SM under the pipeline (0 = automatic)")
     return ap.parse_args()
@@ -402,7 +404,8 @@ def run_async_workload(args, local):
         unit_ns = t_ms * 1e6 / p["f_steps"]
         delays = torch.from_numpy(delay_table(N, 64, seed=p["delay_seed"])).cuda()
     opts = pr.make_async_opts(timeout_s=300.0, delays=delays, delay_unit_ns=unit_ns,
-                              lazy=args.lazy, ctas_per_slice=args.ctas_per_slice)
+                              lazy=args.lazy, ctas_per_slice=args.ctas_per_slice,
+                              verify=args.verify)
     if args.profile:
         code, st, log = pr.parareal_run_async(ctx, opts, lam, log_cap=1 << 20)
         torch.cuda.synchronize()
@@ -459,8 +462,10 @@ def run_async_workload(args, local):
            "config": {"workload": WORKLOADS[args.workload], "grid": list(p["n"]), "N": N,
                       "f_steps": p["f_steps"], "tol": p["tol"],
                       "delay_unit_ns": unit_ns, "delays": delays is not None,
-                      "lazy": bool(args.lazy), "ctas_per_slice": args.ctas_per_slice},
+                      "lazy": bool(args.lazy), "ctas_per_slice": args.ctas_per_slice,
+                      "verify": bool(args.verify)},
            "async": {"status": int(code), "time_to_tol_ms": t_async, "kappa": st.iterations,
+                     "verify_rounds": st.verify_rounds, "residual": st.residual,
                      "events": st.events, "cg_iterations": st.cg_iterations,
                      "fine_cg_iterations": st.fine_cg_iterations,
                      "err_vs_serial_fine": (lam_async - star).abs().max().item() / scale},

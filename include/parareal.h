@@ -110,12 +110,16 @@ typedef struct pr_stats {
   long long events;        /* async: slice updates published */
   long long launches;      /* CUDA kernel launches issued by the call */
   long long fine_cg_iterations; /* CG iterations of the trapezoidal fine steps (2D/3D) */
+  int verify_rounds;       /* async with verify: fixed-point residual checks made */
+  double residual;         /* async with verify: max_i max_x |lam_i - F(lam_{i-1})| at the
+                              last check (0 otherwise) */
 } pr_stats;
 
 /* Asynchronous run options (Algorithm 2). */
 typedef struct pr_async_opts {
   int paper_literal;        /* 1: a slice re-iterates even when its inputs are unchanged */
-  double timeout_s;         /* wall-clock limit of the persistent kernel (e.g. 60) */
+  double timeout_s;         /* wall-clock limit of each launch of the persistent kernel
+                               (e.g. 60; in verify mode every resumed launch gets it anew) */
   const int32_t* delays_dev;/* NULL, or device int32 [N * delay_cols]: publish delay of
                                slice i's e-th update, in units of delay_unit_ns */
   int delay_cols;           /* columns of delays_dev (events beyond it use column e % delay_cols) */
@@ -128,6 +132,15 @@ typedef struct pr_async_opts {
                                input, re-update only when a newer predecessor version
                                appears or the predecessor has settled (skips intermediate
                                updates that a newer version would supersede) */
+  int verify;               /* 1: when the increment rule stops the run (not quiescence),
+                               check the fixed-point residual max_i max_x |lam_i -
+                               F(lam_{i-1})| of the latest versions by one batched F and,
+                               unless it is below tol, resume the kernel with every slice's
+                               last increment forgotten (so each unsettled slice must
+                               publish again); at most 100 checks.  An asynchronous update's
+                               increment can be small while the slice is still far from the
+                               fixed point (its inputs changed little); the check closes
+                               that gap.  The log spans all launches. */
 } pr_async_opts;
 
 /* One asynchronous update event (log entry). */

@@ -97,20 +97,27 @@ class SimResult:
     t_end: float                      # last publication (in-flight updates included)
     stop_reason: str                  # "tol", "quiescent" or "limit"
     n_at_stop: int = 0                # events published when the stop was decided
+    verify_rounds: int = 0            # residual checks made (verify mode)
+    residual: float | None = None     # max_i max|lambda_i - F(lambda_{i-1})| at the last check
     versions: dict = field(default_factory=dict)
 
 
 def async_simulate(prob: dict, workers: int | None = None, c_G: float = 1.0,
                    f_cost: float | None = None, delays=None, tol=None,
                    paper_literal: bool = False, lazy: bool = False, ring: int = 3,
-                   max_updates: int = 100000, u0=None, kappa="from_prob") -> SimResult:
+                   max_updates: int = 100000, verify: bool = False, max_verify: int = 100,
+                   u0=None, kappa="from_prob") -> SimResult:
     """Simulate asynchronous Parareal (Eq. (12), Algorithm 2) on a virtual clock.
 
     workers: number of workers T (default N, one per slice); worker t owns
     slices t+1, t+1+T, ...  c_G, f_cost: costs of one G solve and one F in
     units of one fine step (f_cost defaults to n_f).  delays: (N, cols) array
     of publication delays in the same units (None: no delay).  tol: stop
-    tolerance (default prob["tol"]; 0 runs to quiescence).
+    tolerance (default prob["tol"]; 0 runs to quiescence).  verify: when the
+    increment rule stops the run, check the fixed-point residual
+    max_i max|lambda_i - F(lambda_{i-1})| on the latest versions (one batched F,
+    f_cost units) and resume, with every slice's increment forgotten, unless it
+    is below tol (at most max_verify checks).
     """
     P = Propagators(prob, kappa)
     u0 = prob["u0"] if u0 is None else u0
@@ -197,86 +204,107 @@ def async_simulate(prob: dict, workers: int | None = None, c_G: float = 1.0,
     events = []
     stopped, t_stop, reason, t_last, n_at_stop = False, None, "limit", 0.0, 0
 
-    while heap:
-        t, kind, wk, sq = heapq.heappop(heap)
-        if kind == _DECIDE:
-            if stopped or sq != wake[wk]:
-                continue
-            wake[wk] = None
-            pick = None
-            own = owned[wk]
-            for c in range(len(own)):
-                i = own[(cursor[wk] + c) % len(own)]
-                if has_work(i, t):
-                    pick = i
-                    cursor[wk] = (cursor[wk] + c + 1) % len(own)
-                    break
-            if pick is not None:
-                waiting.discard(wk)
-                job[wk] = dict(i=pick, k=kcount[pick], vF=xver[pick], t0=t)
-                push(t + f_cost, _CHOOSE, wk)
-                continue
-            ok, why = stop_condition()
-            if ok:
-                stopped, t_stop, reason, n_at_stop = True, t, why, len(events)
-                continue
-            # idle: wait for the next visibility instant or publication
-            waiting.add(wk)
-            future = [tv for tv in vis.values() if tv > t]
-            if future:
-                push(min(future), _DECIDE, wk)
-        elif kind == _CHOOSE:
-            jb = job[wk]
-            i, vF = jb["i"], jb["vF"]
-            v = flat(P.F(versions[(i - 1, vF)]))
-            cand = freshest_visible(i - 1, t)
-            vG = cand if cand > vF else vF
-            cg = 0
-            if vG > vF:
-                wn, cg = P.G(versions[(i - 1, vG)], x0=w[i])
-                wn = flat(wn)
-                t_pub = t + c_G
-            else:
-                wn = w[i]
-                t_pub = t
-            new = (wn + v) - w[i]
-            jb.update(vG=vG, wn=wn, new=new, cg=int(cg))
-            push(t_pub, _PUBLISH, wk)
-        else:  # _PUBLISH
-            jb = job[wk]
-            job[wk] = None
-            i, k = jb["i"], jb["k"]
-            d = float(np.max(np.abs(jb["new"] - versions[(i, k)]))) if jb["new"].size else 0.0
-            tv = t + (dl[i - 1, k % dl.shape[1]] if dl is not None else 0.0)
-            versions[(i, k + 1)] = jb["new"]
-            vis[(i, k + 1)] = tv
-            latest[i] = k + 1
-            delta[i] = d
-            xver[i] = jb["vG"]
-            lastfg[i] = jb["vG"] == jb["vF"]
-            kcount[i] = k + 1
-            w[i] = jb["wn"]
-            events.append(SimEvent(i, k + 1, jb["vF"], jb["vG"], wk, jb["t0"], t, tv, d, jb["cg"]))
-            t_last = t
-            if stopped:
-                continue
-            ok, why = stop_condition()
-            if ok:
-                stopped, t_stop, reason, n_at_stop = True, t, why, len(events)
-            elif len(events) >= max_updates:
-                stopped, t_stop, reason, n_at_stop = True, t, "limit", len(events)
-            else:
-                push(t, _DECIDE, wk)
-                for other in sorted(waiting):
-                    push(t, _DECIDE, other)
-                waiting.clear()
+    verify_rounds, residual = 0, None
+    while True:
+        while heap:
+            t, kind, wk, sq = heapq.heappop(heap)
+            if kind == _DECIDE:
+                if stopped or sq != wake[wk]:
+                    continue
+                wake[wk] = None
+                pick = None
+                own = owned[wk]
+                for c in range(len(own)):
+                    i = own[(cursor[wk] + c) % len(own)]
+                    if has_work(i, t):
+                        pick = i
+                        cursor[wk] = (cursor[wk] + c + 1) % len(own)
+                        break
+                if pick is not None:
+                    waiting.discard(wk)
+                    job[wk] = dict(i=pick, k=kcount[pick], vF=xver[pick], t0=t)
+                    push(t + f_cost, _CHOOSE, wk)
+                    continue
+                ok, why = stop_condition()
+                if ok:
+                    stopped, t_stop, reason, n_at_stop = True, t, why, len(events)
+                    continue
+                # idle: wait for the next visibility instant or publication
+                waiting.add(wk)
+                future = [tv for tv in vis.values() if tv > t]
+                if future:
+                    push(min(future), _DECIDE, wk)
+            elif kind == _CHOOSE:
+                jb = job[wk]
+                i, vF = jb["i"], jb["vF"]
+                v = flat(P.F(versions[(i - 1, vF)]))
+                cand = freshest_visible(i - 1, t)
+                vG = cand if cand > vF else vF
+                cg = 0
+                if vG > vF:
+                    wn, cg = P.G(versions[(i - 1, vG)], x0=w[i])
+                    wn = flat(wn)
+                    t_pub = t + c_G
+                else:
+                    wn = w[i]
+                    t_pub = t
+                new = (wn + v) - w[i]
+                jb.update(vG=vG, wn=wn, new=new, cg=int(cg))
+                push(t_pub, _PUBLISH, wk)
+            else:  # _PUBLISH
+                jb = job[wk]
+                job[wk] = None
+                i, k = jb["i"], jb["k"]
+                d = float(np.max(np.abs(jb["new"] - versions[(i, k)]))) if jb["new"].size else 0.0
+                tv = t + (dl[i - 1, k % dl.shape[1]] if dl is not None else 0.0)
+                versions[(i, k + 1)] = jb["new"]
+                vis[(i, k + 1)] = tv
+                latest[i] = k + 1
+                delta[i] = d
+                xver[i] = jb["vG"]
+                lastfg[i] = jb["vG"] == jb["vF"]
+                kcount[i] = k + 1
+                w[i] = jb["wn"]
+                events.append(SimEvent(i, k + 1, jb["vF"], jb["vG"], wk, jb["t0"], t, tv, d, jb["cg"]))
+                t_last = t
+                if stopped:
+                    continue
+                ok, why = stop_condition()
+                if ok:
+                    stopped, t_stop, reason, n_at_stop = True, t, why, len(events)
+                elif len(events) >= max_updates:
+                    stopped, t_stop, reason, n_at_stop = True, t, "limit", len(events)
+                else:
+                    push(t, _DECIDE, wk)
+                    for other in sorted(waiting):
+                        push(t, _DECIDE, other)
+                    waiting.clear()
 
-    if not stopped:
-        # every worker idle, nothing in flight and nothing left to become visible
-        ok, why = stop_condition()
-        if not ok:
-            raise RuntimeError("no worker can make progress and the stop rule does not hold")
-        t_stop, reason, n_at_stop = t_last, why, len(events)
+        if not stopped:
+            # every worker idle, nothing in flight and nothing left to become visible
+            ok, why = stop_condition()
+            if not ok:
+                raise RuntimeError("no worker can make progress and the stop rule does not hold")
+            t_stop, reason, n_at_stop = t_last, why, len(events)
+
+        if not verify or reason != "tol":
+            break
+        # residual of the fixed point lambda_i = F(lambda_{i-1}) on the latest
+        # versions: one batched F, f_cost units after the last publication
+        cur = [versions[(i, latest[i])] for i in range(N + 1)]
+        residual = max(float(np.max(np.abs(cur[i] - flat(P.F(cur[i - 1])))))
+                       for i in range(1, N + 1))
+        verify_rounds += 1
+        t_last = max(t_last, t_stop) + f_cost
+        if residual < tol or verify_rounds >= max_verify:
+            break
+        # resume: every unsettled slice must publish again before the rule fires
+        for i in range(1, N + 1):
+            delta[i] = np.inf
+        stopped, t_stop, reason = False, None, "limit"
+        waiting.clear()
+        for wk in range(T):
+            push(t_last, _DECIDE, wk)
 
     M = versions[(0, 0)].size
     lam = np.zeros((N + 1, M))
@@ -286,4 +314,4 @@ def async_simulate(prob: dict, workers: int | None = None, c_G: float = 1.0,
     return SimResult(events=events, lam=lam, k_i=k_i, kappa=int(k_i.max()) if N else 0,
                      updates=len(events), t_stop=t_stop if t_stop is not None else t_last,
                      t_end=t_last, stop_reason=reason, n_at_stop=n_at_stop,
-                     versions=versions)
+                     verify_rounds=verify_rounds, residual=residual, versions=versions)

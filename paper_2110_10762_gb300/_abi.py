@@ -33,7 +33,8 @@ class pr_stats(C.Structure):
                 ("fine_lups", C.c_longlong), ("cg_iterations", C.c_longlong),
                 ("coarse_solves", C.c_longlong), ("t_total_ms", C.c_double),
                 ("t_fine_ms", C.c_double), ("t_coarse_ms", C.c_double), ("events", C.c_longlong),
-                ("launches", C.c_longlong), ("fine_cg_iterations", C.c_longlong)]
+                ("launches", C.c_longlong), ("fine_cg_iterations", C.c_longlong),
+                ("verify_rounds", C.c_int), ("residual", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -43,7 +44,7 @@ class pr_async_opts(C.Structure):
     _fields_ = [("paper_literal", C.c_int), ("timeout_s", C.c_double),
                 ("delays_dev", C.c_void_p), ("delay_cols", C.c_int),
                 ("delay_unit_ns", C.c_double), ("ctas_per_slice", C.c_int),
-                ("quiescence", C.c_int), ("lazy", C.c_int)]
+                ("quiescence", C.c_int), ("lazy", C.c_int), ("verify", C.c_int)]
 
 
 class pr_event(C.Structure):

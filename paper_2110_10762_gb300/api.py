@@ -143,7 +143,8 @@ def parareal_correct(ctx, w_new, v, w_old, lam_inout) -> float:
 
 
 def make_async_opts(paper_literal=False, timeout_s=60.0, delays=None, delay_unit_ns=0.0,
-                    ctas_per_slice=0, quiescence=False, lazy=False) -> pr_async_opts:
+                    ctas_per_slice=0, quiescence=False, lazy=False,
+                    verify=False) -> pr_async_opts:
     o = pr_async_opts()
     o.paper_literal = int(bool(paper_literal))
     o.timeout_s = float(timeout_s)
@@ -157,6 +158,7 @@ def make_async_opts(paper_literal=False, timeout_s=60.0, delays=None, delay_unit
     o.ctas_per_slice = int(ctas_per_slice)
     o.quiescence = int(bool(quiescence))
     o.lazy = int(bool(lazy))
+    o.verify = int(bool(verify))
     return o
 
 

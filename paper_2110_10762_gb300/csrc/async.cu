@@ -525,6 +525,22 @@ __global__ void async_init(AsyncDev a) {
   (void)M;
 }
 
+constexpr int ASYNC_MAX_VERIFY = 100;  // residual checks of one run (verify mode)
+
+// out <- bits of max_p |a_p - b_p| over n values (non-negative doubles order
+// like their bit patterns); out must be zero beforehand.
+__global__ void resid_kernel(const double* __restrict__ a, const double* __restrict__ b,
+                             long long n, unsigned long long* out) {
+  unsigned long long m = 0ull;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long d = abs_bits(a[i] - b[i]);
+    m = d > m ? d : m;
+  }
+  m = warp_max_u64(m);
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
 // lam_out row i <- slice i's latest version (row 0 = u0 already there).
 __global__ void async_gather(AsyncDev a, double* lam) {
   const long long M = a.g.M;
@@ -718,26 +734,52 @@ int run_async(pr_ctx* c, const pr_async_opts* o, double* lam, pr_stats* st, pr_e
 
   a.timeout_ns = (unsigned long long)(o->timeout_s * 1e9);
 
-  // the persistent kernel: all T*C blocks co-resident (cooperative launch)
+  // the persistent kernel: all T*C blocks co-resident (cooperative launch).  In
+  // verify mode a stop by the increment rule is followed by a check of the
+  // fixed-point residual max_i |lam_i - F(lam_{i-1})| on the latest versions
+  // (one batched F into the sync workspace v); unless it is below tol the
+  // kernel resumes from its persistent state with every slice's increment
+  // forgotten (NaN: "not below"), so each unsettled slice publishes again.
   PR_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
   void* args[] = {&a};
-  cudaError_t e = cudaLaunchCooperativeKernel((void*)async_kernel, dim3(T * C), dim3(ATHREADS), args,
-                                              0, c->stream);
-  if (e != cudaSuccess) {
-    if (dlog) cudaFree(dlog);
-    return cuda_fail(c, e, "async kernel launch");
-  }
-  ++launches;
-  PR_CUDA(c, cudaEventRecord(c->ev[2], c->stream));
-  async_gather<<<dim3(64, std::min(N, 64)), 256, 0, c->stream>>>(a, lam);
-  ++launches;
-  PR_CUDA(c, cudaEventRecord(c->ev[3], c->stream));
   int flags[3] = {0, 0, 0};
+  int rounds = 0;
+  double resid = 0.0;
+  for (;;) {
+    cudaError_t e = cudaLaunchCooperativeKernel((void*)async_kernel, dim3(T * C), dim3(ATHREADS),
+                                                args, 0, c->stream);
+    if (e != cudaSuccess) {
+      if (dlog) cudaFree(dlog);
+      return cuda_fail(c, e, "async kernel launch");
+    }
+    ++launches;
+    async_gather<<<dim3(64, std::min(N, 64)), 256, 0, c->stream>>>(a, lam);
+    ++launches;
+    PR_CUDA(c, cudaMemcpyAsync(flags, a.stop, 3 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    PR_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (!o->verify || o->quiescence || flags[1] != AST_OK || flags[2]) break;
+    PR_CUDA(c, fine_apply(c, lam, c->v, N));
+    launches += (p.f_scheme == PR_EXPLICIT_EULER) ? p.f_steps : 1;
+    PR_CUDA(c, cudaMemsetAsync(c->delta_dev, 0, sizeof(unsigned long long), c->stream));
+    resid_kernel<<<c->num_sms * 4, 256, 0, c->stream>>>(lam + M, c->v, (long long)N * M,
+                                                         c->delta_dev);
+    ++launches;
+    unsigned long long rbits = 0;
+    PR_CUDA(c, cudaMemcpyAsync(&rbits, c->delta_dev, sizeof rbits, cudaMemcpyDeviceToHost,
+                               c->stream));
+    PR_CUDA(c, cudaStreamSynchronize(c->stream));
+    memcpy(&resid, &rbits, sizeof resid);
+    ++rounds;
+    if (resid < p.tol || rounds >= ASYNC_MAX_VERIFY) break;
+    PR_CUDA(c, cudaMemsetAsync(a.delta, 0xFF, (size_t)N * sizeof(double), c->stream));
+    PR_CUDA(c, cudaMemsetAsync(a.stop, 0, sizeof(int), c->stream));
+  }
+  PR_CUDA(c, cudaEventRecord(c->ev[2], c->stream));
+  PR_CUDA(c, cudaEventRecord(c->ev[3], c->stream));
   unsigned long long nlog = 0, fine_cg = 0;
   PR_CUDA(c, cudaMemcpyAsync(&fine_cg, a.fine_cg, sizeof fine_cg, cudaMemcpyDeviceToHost, c->stream));
   std::vector<int> kc(N);
   std::vector<double> dl(N);
-  PR_CUDA(c, cudaMemcpyAsync(flags, a.stop, 3 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   PR_CUDA(c, cudaMemcpyAsync(&nlog, a.log_count, sizeof nlog, cudaMemcpyDeviceToHost, c->stream));
   PR_CUDA(c, cudaMemcpyAsync(kc.data(), a.kcount, N * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   PR_CUDA(c, cudaMemcpyAsync(dl.data(), a.delta, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -776,7 +818,9 @@ int run_async(pr_ctx* c, const pr_async_opts* o, double* lam, pr_stats* st, pr_e
   S.launches = launches;
   S.fine_cg_iterations = (long long)fine_cg;
   const int status = flags[1], berr = flags[2];
-  S.converged = (status == AST_OK && !berr) ? 1 : 0;
+  S.converged = (status == AST_OK && !berr && (rounds == 0 || resid < p.tol)) ? 1 : 0;
+  S.verify_rounds = rounds;
+  S.residual = rounds ? resid : 0.0;
   if (st) *st = S;
   if (berr || status == AST_BARRIER) return fail(c, PR_ETIMEOUT, "async: a bounded barrier wait expired");
   if (status == AST_TIMEOUT) return fail(c, PR_ETIMEOUT, "async: wall-clock limit reached");

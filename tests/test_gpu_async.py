@@ -144,6 +144,30 @@ def test_async_lazy_policy(quiescence):
         assert rel_l2(lam, serial_fine(p)) < FP64_TOL
 
 
+@pytest.mark.parametrize("name", ["heat2d_explicit", "heat3d_varkappa_async"])
+def test_async_verified_stop(name):
+    """Verify mode: the run ends only when the fixed-point residual
+    max_i |lam_i - F(lam_{i-1})| of the latest versions is below tol (checked
+    here with the oracle's F); the log spans every resumed launch and replays
+    to the same state.  One team per slice (lockstep-like schedule)."""
+    from oracle import heat
+
+    p = case(name, tol=1e-9)
+    with Ctx(p) as c:
+        code, st, log, lam = run_async(c, timeout_s=60.0, verify=True, ctas_per_slice=8)
+    assert code == pr.PR_OK and st.converged and st.verify_rounds >= 1
+    assert st.residual < p["tol"]
+    check_log(log, p["N"])
+    assert st.events == len(log)
+    P = heat.Propagators(p)
+    L = lam.reshape((p["N"] + 1,) + tuple(reversed(p["n"])))
+    scale = np.max(np.abs(L))
+    res = max(np.max(np.abs(L[i] - P.F(L[i - 1]))) for i in range(1, p["N"] + 1))
+    assert res < p["tol"] + 1e-13 * scale, res
+    rep = async_replay(p, events_of(log))
+    assert rel_l2(lam, rep.lam) < FP64_TOL
+
+
 def test_async_paper_literal_mode():
     p = case("heat2d_explicit", tol=1e-9)
     with Ctx(p) as c:

@@ -166,3 +166,28 @@ def test_rejects_bad_arguments():
         async_simulate(prob, c_G=-1.0)
     with pytest.raises(ValueError):
         async_simulate(prob, delays=np.zeros((3, 2)))
+
+
+def test_verified_stop_closes_the_increment_gap():
+    """A delay-free lockstep schedule (one worker per slice) on a slowly
+    contracting problem: the per-slice increment rule stops while the state is
+    still far from the fixed point (error 100x tol); with the residual check the
+    run resumes until max_i |lambda_i - F(lambda_{i-1})| < tol, and the error
+    falls to the order of tol."""
+    prob = small_prob(1, (31,), N=32, f_steps=20, dt_h2=1.0, f_scheme="implicit")
+    tol = 1e-6
+    ref = serial_fine(prob)
+    scale = np.max(np.abs(ref))
+    plain = async_simulate(prob, c_G=0.2, tol=tol)
+    assert plain.stop_reason == "tol"
+    assert np.max(np.abs(plain.lam - ref)) > 10 * tol * scale
+    checked = async_simulate(prob, c_G=0.2, tol=tol, verify=True)
+    assert checked.verify_rounds >= 2 and checked.residual < tol
+    P = __import__("oracle.heat", fromlist=["Propagators"]).Propagators(prob)
+    res = max(np.max(np.abs(checked.lam[i] - P.F(checked.lam[i - 1])))
+              for i in range(1, prob["N"] + 1))
+    assert res == checked.residual
+    assert np.max(np.abs(checked.lam - ref)) < tol * scale
+    # the resumed run is still one valid asynchronous schedule
+    rep = async_replay(prob, checked.events)
+    np.testing.assert_array_equal(rep.lam, checked.lam)
