@@ -15,7 +15,7 @@ from synthetic import preset
 
 from .gpu_util import Ctx, dev, host, rel_l2, torch
 
-pr = pytest.importorskip("paper_2110_10762_gb300")
+import paper_2110_10762_gb300 as pr  # noqa: E402  (a missing library fails the first call loudly)
 
 pytestmark = pytest.mark.gpu
 

@@ -13,7 +13,7 @@ This file is collected last on purpose.
 import numpy as np
 import pytest
 
-pr = pytest.importorskip("paper_2110_10762_gb300")
+import paper_2110_10762_gb300 as pr  # noqa: E402  (a missing library fails the first call loudly)
 
 pytestmark = pytest.mark.gpu
 
