@@ -84,3 +84,29 @@ def test_null_context_calls_are_rejected(lib_path):
     assert lib.parareal_set_problem(None, None) == _abi.PR_EINVAL
     assert lib.parareal_run_sync(None, None, None) == _abi.PR_EINVAL
     assert lib.parareal_create(None, 0, None) == _abi.PR_EINVAL
+
+
+def test_python_struct_layouts_match_the_header(tmp_path):
+    """Compile a probe against include/parareal.h and compare sizeof / offsetof of
+    every field of the public structs with the ctypes view the binding uses."""
+    from paper_2110_10762_gb300 import _abi
+    structs = {"pr_problem": _abi.pr_problem, "pr_stats": _abi.pr_stats,
+               "pr_async_opts": _abi.pr_async_opts, "pr_event": _abi.pr_event}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", f'#include "{HEADER}"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'  printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "probe.c"
+    exe = tmp_path / "probe"
+    src.write_text("\n".join(lines) + "\n")
+    subprocess.run(["gcc", "-std=c11", "-o", str(exe), str(src)], check=True)
+    got = {}
+    for ln in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        s, f, v = ln.split()
+        got[(s, f)] = int(v)
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)
