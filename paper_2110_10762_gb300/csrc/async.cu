@@ -799,6 +799,9 @@ int run_async(pr_ctx* c, const pr_async_opts* o, double* lam, pr_stats* st, pr_e
   int kmax = 0;
   double dmax = 0.0;
   for (int i = 0; i < N; ++i) {
+    // a slice that published nothing after the last residual check (verify
+    // mode) was settled: another update would not move it
+    if (std::isnan(dl[i])) dl[i] = 0.0;
     c->last_k[i] = kc[i];
     c->last_delta[i] = dl[i];
     kmax = std::max(kmax, kc[i]);
