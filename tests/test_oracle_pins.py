@@ -240,6 +240,24 @@ def test_cg_solves_backward_euler(dim):
     np.testing.assert_allclose(xm, u / (1 + dT * mu), rtol=1e-12, atol=1e-14)
 
 
+@pytest.mark.parametrize("n", [(40, 33), (12, 10, 9)])
+def test_cg_matches_the_sine_transform_solution(n):
+    """Constant kappa: I + dT A is diagonal in the type-I sine basis (each grid
+    axis separately), so the exact backward-Euler step of a random right-hand
+    side is DST^-1[DST(b) / (1 + dT mu)] (scipy's FFT-based DST-I, an
+    independent route).  The oracle's CG meets it at rtol 1e-14."""
+    h = tuple(1.0 / (m + 1) for m in n)
+    shape = tuple(reversed(n))
+    rng = np.random.default_rng(21)
+    b = rng.standard_normal(shape)
+    dT = 60 * min(h) ** 2
+    mu = grid_mu(n, h)
+    exact = scipy.fft.idstn(scipy.fft.dstn(b, type=1) / (1 + dT * mu), type=1)
+    x, it = heat.cg_implicit_euler(b, dT, h, None, None, rtol=1e-14, maxit=2000)
+    assert np.linalg.norm(x - exact) / np.linalg.norm(exact) < 1e-12
+    assert it > 10
+
+
 @pytest.mark.parametrize("m", [2, 5, 8])
 def test_chebyshev_preconditioner_on_a_mode(m):
     """On an eigenvector of B = I + dT A with eigenvalue lam, m Chebyshev steps give
