@@ -26,6 +26,9 @@
 // updated at least once and its last increment is below tol, or when no
 // slice can change any more (quiescence: lam_i = F(lam_{i-1}) for all i),
 // or at the wall-clock limit (status PR_ETIMEOUT).  Every spin is bounded.
+// Optionally (verify mode) the host confirms a stop by the increment rule with
+// the fixed-point residual max_i |lam_i - F(lam_{i-1})| (one batched F) and
+// relaunches the kernel on its persistent state when the residual is too large.
 #include <string.h>
 
 #include <algorithm>
