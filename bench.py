@@ -124,6 +124,13 @@ def sync_delay_ms(table, unit_ns, k, N):
     return units * unit_ns / 1e6
 
 
+def apr_cost(p, kappa, C_F, C_G):
+    """Proposition 3 (§4.1): cost of kappa(k~) asynchronous iterations with one
+    processor per slice and communication fully overlapped,
+        C~ = p C_G + kappa (C_F + C_G)."""
+    return p * C_G + kappa * (C_F + C_G)
+
+
 def cost_model_async(log, N, t_ms):
     """Per-update costs of an asynchronous run read from its event log (§4.1,
     Proposition 3 charges kappa (C_F + C_G) per processor): the mean duration
@@ -139,6 +146,16 @@ def cost_model_async(log, N, t_ms):
     return {"p": N, "kappa": max(k_i.values()) if k_i else 0, "updates": len(log),
             "update_F_ms": mean(f_only), "update_FG_ms": mean(f_g),
             "n_F_only": len(f_only), "n_FG": len(f_g), "measured_ms": t_ms}
+
+
+def cost_models(log, N, t_async, p, sync_stats, t_sync):
+    """Both cost models on one problem, plus Proposition 3's estimate of the
+    asynchronous time from the synchronous run's C_F and C_G (the model's one
+    processor per slice, each F as fast as one batched fine phase)."""
+    a = cost_model_async(log, N, t_async)
+    sm = cost_model_sync(p, sync_stats, t_sync)
+    a["prop3_ms"] = apr_cost(N, a["kappa"], sm["C_F_ms"], sm["C_G_ms"])
+    return {"async": a, "sync": sm}
 
 
 def parse():
@@ -477,8 +494,7 @@ def run_async_workload(args, local):
            "sync_with_same_delays_ms": (t_sync + sync_delay_ms(delay_table(N, 64, seed=p["delay_seed"]),
                                                                unit_ns, sst.iterations, N)
                                         if delays is not None else None),
-           "cost_model": {"async": cost_model_async(log, N, t_async),
-                          "sync": cost_model_sync(p, sst.as_dict(), t_sync)},
+           "cost_model": cost_models(log, N, t_async, p, sst.as_dict(), t_sync),
            "kappa_over_k": st.iterations / max(sst.iterations, 1),
            "roofline": roof, "gpu_launches": launches, "clocks": clk.summary()}
     print(json.dumps(out), flush=True)

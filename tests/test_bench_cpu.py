@@ -26,6 +26,11 @@ def test_async_cost_model_reads_the_log():
     assert cm["kappa"] == 2 and cm["updates"] == 3
     assert cm["update_F_ms"] == 4.0 and cm["update_FG_ms"] == 5.0
     assert cm["n_F_only"] == 2 and cm["n_FG"] == 1
+    both = bench.cost_models(log, 2, 9.0, {"N": 2},
+                             {"iterations": 1, "coarse_solves": 3, "t_fine_ms": 4.0,
+                              "t_coarse_ms": 3.0}, 8.0)
+    assert both["async"]["prop3_ms"] == bench.apr_cost(2, 2, 4.0, 1.0) == 12.0
+    assert both["sync"]["C_F_ms"] == 4.0 and both["sync"]["C_G_ms"] == 1.0
 
 
 def test_sync_delay_sums_the_updated_slices():
@@ -58,3 +63,18 @@ def test_reference_arm_prints_one_contract_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert "workload" in d["config"]
+
+
+def test_proposition3_reproduces_the_papers_table1_estimates():
+    """The bench's Proposition 3 (C~ = p C_G + kappa (C_F + C_G)) with the paper's
+    C_G = 0.14 s and C_F = 100 C_G gives Table 1's printed estimates: within
+    0.1% for five rows, 1.4% for p = 16 (whose kappa is a rounded average)."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "table1_async_cost.txt")
+    rows = [ln.split() for ln in open(path) if ln[0].isdigit()]
+    assert len(rows) == 6
+    C_G = 0.14
+    for p, kappa, printed in rows:
+        est = bench.apr_cost(int(p), int(kappa), 100 * C_G, C_G)
+        tol = 0.015 if p == "16" else 0.001
+        assert abs(est - float(printed)) <= tol * float(printed), (p, est, printed)
