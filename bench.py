@@ -355,6 +355,8 @@ def mixed_vs_fp64(pr, torch, p, u0, lam_mixed, t_mixed_ms, args, local):
     try:
         prob = problem_struct(pr, p, u0, None, f_prec=64)
         pr.parareal_set_problem(ctx, prob)
+        if args.g_cheb:
+            pr.parareal_set_option(ctx, pr.PR_OPT_G_CHEBYSHEV, args.g_cheb)
         lam64 = torch.empty_like(lam_mixed)
         for _ in range(max(1, min(args.warmup, 1))):
             pr.parareal_run_sync(ctx, lam64)

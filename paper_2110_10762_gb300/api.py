@@ -204,10 +204,31 @@ def parareal_slice_stats(ctx, N: int):
 def parareal_coarse_noalloc(dim: int, n, dT: float, b, x0, x_out, rtol: float = 1e-10,
                             maxit: int = 0, stream=None) -> int:
     """Allocation-free coarse solve (kappa = 1) for callers that must not allocate
-    device memory; see include/parareal.h.  Returns the CG iteration count."""
-    if stream is not None and not isinstance(stream, int):
+    device memory; see include/parareal.h.  Returns the CG iteration count.
+
+    The wrapper checks that dim matches len(n) and that b, x0 (if given) and
+    x_out hold at least prod(n) float64 values before the library sees the
+    pointers (the C entry point cannot know the buffers' lengths).  With
+    stream=None the work goes on torch's current stream, like the context path."""
+    import torch
+    n = [int(v) for v in n]
+    if not 1 <= int(dim) == len(n) <= 3:
+        raise ValueError("dim must equal len(n) and lie in 1..3 (dim=%r, n=%r)" % (dim, n))
+    M = 1
+    for v in n:
+        M *= v
+    for name, t in (("b", b), ("x0", x0), ("x_out", x_out)):
+        if t is None and name == "x0":
+            continue
+        if t is None or t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous CUDA float64 tensor")
+        if t.numel() < M:
+            raise ValueError(f"{name} holds {t.numel()} values, fewer than prod(n) = {M}")
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    if not isinstance(stream, int):
         stream = stream.cuda_stream
-    nn = (C.c_int * 3)(*(list(n) + [1] * (3 - len(n))))
+    nn = (C.c_int * 3)(*(n + [1] * (3 - len(n))))
     it = C.c_int(0)
     code = _lib().parareal_coarse_noalloc(int(dim), nn, float(dT), _ptr(b), _ptr(x0), _ptr(x_out),
                                           float(rtol), int(maxit), C.byref(it), stream)

@@ -177,11 +177,21 @@ int parareal_set_problem(pr_ctx* c, const pr_problem* pin) {
   free_problem(c);
   pr_problem p = *pin;
   if (p.dim < 1 || p.dim > 3) return fail(c, PR_EINVAL, "dim must be 1, 2 or 3");
+  // each axis, then the running product, is bounded before the next
+  // multiplication, so no product of large axes can overflow past the limits
+  long long m_points = 1;
   for (int a = 0; a < 3; ++a) {
     if (a >= p.dim) p.n[a] = 1;
     if (p.n[a] < 1) return fail(c, PR_EINVAL, "every n[a] must be >= 1");
+    if (p.n[a] > PR_MAX_POINTS) return fail(c, PR_EINVAL, "n[a] exceeds the point limit");
+    m_points *= p.n[a];
+    if (m_points > PR_MAX_POINTS)
+      return fail(c, PR_EINVAL, "prod(n) exceeds the point limit (2^31 - 1 per state)");
   }
   if (p.N < 1) return fail(c, PR_EINVAL, "N must be >= 1");
+  if (p.N > PR_MAX_SLICES) return fail(c, PR_EINVAL, "N exceeds the slice limit (65536)");
+  if ((long long)(p.N + 1) > PR_MAX_TRAJ_POINTS / m_points)
+    return fail(c, PR_EINVAL, "(N+1) * prod(n) exceeds the trajectory limit (2^40 points)");
   if (!(p.T > p.T0)) return fail(c, PR_EINVAL, "T must exceed T0");
   if (p.f_steps < 1) return fail(c, PR_EINVAL, "f_steps must be >= 1");
   if (p.f_scheme != PR_EXPLICIT_EULER && p.f_scheme != PR_IMPLICIT_EULER &&

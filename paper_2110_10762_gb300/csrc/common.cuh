@@ -11,6 +11,13 @@
 
 namespace pr {
 
+// Size limits checked by parareal_set_problem: points per state (the kernels
+// index rows and planes with 32-bit integers), slices, and points of the
+// stacked (N+1)-state trajectory.
+constexpr long long PR_MAX_POINTS = 2147483647LL;
+constexpr int PR_MAX_SLICES = 65536;
+constexpr long long PR_MAX_TRAJ_POINTS = 1LL << 40;
+
 // Grid geometry of one state (interior points only), x fastest.
 struct Geom {
   int dim;

@@ -74,20 +74,57 @@ __global__ void __launch_bounds__(NOALLOC_THREADS) noalloc_cg_kernel(NoallocArgs
 struct DeviceSetup {
   double* scratch = nullptr;
   int max_blocks = 0;
+  unsigned long long ctx_id = 0;  // context the address was resolved in (0: unknown)
   bool ready = false;
 };
 
 std::mutex g_setup_mutex;
 DeviceSetup g_setup[128];
 
-// Once per device, with that device current: resolve the array's device
-// address (the host-side symbol is only a stand-in and must never be passed
-// to a kernel) and the co-resident block limit of the cooperative kernel.
+typedef int (*CtxGetCurrentFn)(void**);
+typedef int (*CtxGetIdFn)(void*, unsigned long long*);
+
+// Identity of the calling thread's current context, or 0 when the driver does
+// not report one.  A device's primary context gets a new identity when it is
+// recreated (after cudaDeviceReset), and the module holding the array is then
+// loaded again, possibly at another address: the set-up below is redone.
+unsigned long long current_context_id() {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) ==
+            cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) ==
+            cudaSuccess &&
+        q2 == cudaDriverEntryPointSuccess) {
+      get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+      get_id = reinterpret_cast<CtxGetIdFn>(f2);
+    }
+    looked_up = true;
+  }
+  if (!get_current || !get_id) return 0;
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+  return id;
+}
+
+// Once per device (and again if the device's context was recreated), with
+// that device current: resolve the array's device address (the host-side
+// symbol is only a stand-in and must never be passed to a kernel) and the
+// co-resident block limit of the cooperative kernel.
 cudaError_t setup_current_device(int dev, DeviceSetup** out) {
   if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_setup_mutex);
   DeviceSetup& s = g_setup[dev];
-  if (!s.ready) {
+  const unsigned long long ctx_id = current_context_id();
+  if (!s.ready || s.ctx_id != ctx_id) {
+    s.ready = false;
     void* ptr = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
@@ -98,6 +135,7 @@ cudaError_t setup_current_device(int dev, DeviceSetup** out) {
     if (e != cudaSuccess) return e;
     s.scratch = static_cast<double*>(ptr);
     s.max_blocks = sms * (per_sm > 0 ? per_sm : 1);
+    s.ctx_id = ctx_id;
     s.ready = true;
   }
   *out = &s;
@@ -115,12 +153,14 @@ extern "C" int parareal_coarse_noalloc(int dim, const int* n, double dT, const d
     return PR_EINVAL;
   long long M = 1;
   int nn[3] = {1, 1, 1};
+  // each axis and the running product are checked before the next multiplication,
+  // so no product of large axes can overflow past the limit
   for (int a = 0; a < dim; ++a) {
-    if (n[a] < 1) return PR_EINVAL;
+    if (n[a] < 1 || n[a] > NOALLOC_MAX_POINTS) return PR_EINVAL;
     nn[a] = n[a];
     M *= n[a];
+    if (M > NOALLOC_MAX_POINTS) return PR_EINVAL;  // beyond the static scratch: rejected
   }
-  if (M > NOALLOC_MAX_POINTS) return PR_EINVAL;  // beyond the static scratch: rejected
   if ((((uintptr_t)b_dev | (uintptr_t)x_dev | (uintptr_t)x0_dev) & 15u) != 0) return PR_EINVAL;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return PR_ECUDA;

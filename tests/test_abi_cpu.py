@@ -110,3 +110,22 @@ def test_python_struct_layouts_match_the_header(tmp_path):
         assert got[(name, "size")] == ctypes.sizeof(cls), name
         for field, _ in cls._fields_:
             assert got[(name, field)] == getattr(cls, field).offset, (name, field)
+
+
+def test_noalloc_size_check_rejects_large_axes_without_overflow(lib_path):
+    """parareal_coarse_noalloc bounds each axis and the running product before
+    multiplying: three axes whose product wraps a 64-bit integer (2^21 each:
+    2^63) or lands back under the limit must be rejected, as must a single
+    axis beyond it.  The size check precedes every CUDA call and never
+    dereferences the (fake, aligned, non-null) pointers."""
+    from paper_2110_10762_gb300 import _abi
+    lib = _abi.load(lib_path)
+    fake = ctypes.c_void_p(256)
+    it = ctypes.c_int(0)
+    for n in [(1 << 21, 1 << 21, 1 << 21), (1 << 31) - 1, (131073,), (65536, 65536, 4),
+              (2, 65537), (3000000000 % (1 << 31), 1, 1)]:
+        n = n if isinstance(n, tuple) else (n, n, n)
+        nn = (ctypes.c_int * 3)(*(list(n) + [1] * (3 - len(n))))
+        code = lib.parareal_coarse_noalloc(len(n), nn, 1e-3, fake, None, fake, 1e-10, 0,
+                                           ctypes.byref(it), None)
+        assert code == _abi.PR_EINVAL, n

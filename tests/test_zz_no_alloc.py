@@ -47,15 +47,32 @@ def test_noalloc_coarse_matches_context_coarse_twice():
             got = torch.full_like(b, float("nan"))
             it = pr.parareal_coarse_noalloc(2, n, dT, b, x0, got, rtol=1e-13, stream=stream)
             torch.cuda.synchronize()
-            assert it == it_ref, (call, it, it_ref)
+            # the two kernels may run with different block counts, which changes the
+            # order of the FP64 reductions: the stop test may fall one iteration apart
+            assert abs(it - it_ref) <= 1, (call, it, it_ref)
             assert _rel(got.cpu().numpy(), ref.cpu().numpy()) < FP64_TOL, call
     finally:
         pr.parareal_destroy(ctx)
 
 
 def test_noalloc_rejects_grids_beyond_its_limit():
+    """A grid one point beyond the 131072-point limit is rejected before any
+    launch; the buffers hold the full declared size, so the call could not
+    fault even if the limit were raised."""
     import torch
-    b = torch.zeros(8, dtype=torch.float64, device="cuda")
+    M = 131073
+    b = torch.zeros(M, dtype=torch.float64, device="cuda")
+    x = torch.zeros(M, dtype=torch.float64, device="cuda")
     with pytest.raises(pr.PararealError) as e:
-        pr.parareal_coarse_noalloc(2, (1024, 1024), 1e-3, b, None, b)
+        pr.parareal_coarse_noalloc(1, (M,), 1e-3, b, None, x)
     assert e.value.code == pr.PR_EINVAL
+
+
+def test_noalloc_wrapper_rejects_short_buffers_and_mismatched_dims():
+    import torch
+    b = torch.zeros(100, dtype=torch.float64, device="cuda")
+    x = torch.zeros(100, dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        pr.parareal_coarse_noalloc(2, (11, 10), 1e-3, b, None, x)   # 110 > 100 values
+    with pytest.raises(ValueError):
+        pr.parareal_coarse_noalloc(2, (10, 10, 1), 1e-3, b, None, x)  # dim != len(n)
