@@ -195,6 +195,59 @@ def cg_implicit_euler(b: np.ndarray, dt: float, h, kappa=None, x0=None,
     return x, it
 
 
+def cg1_implicit_euler(b: np.ndarray, dt: float, h, kappa=None, x0=None,
+                       rtol: float = 1e-10, maxit: int = 10000):
+    """One backward-Euler step (I + dt A) x = b by single-reduction conjugate
+    gradients (Chronopoulos and Gear, 1989): the same Krylov iterates as the
+    textbook CG above in exact arithmetic, with both inner products of an
+    iteration taken together on the residual,
+
+        r_0 = b - B x_0,  w_0 = B r_0,  gamma_0 = (r_0, r_0),  delta_0 = (w_0, r_0),
+        alpha_0 = gamma_0 / delta_0,  beta_0 = 0,  p_{-1} = s_{-1} = 0,
+        p_i = r_i + beta_i p_{i-1},      s_i = w_i + beta_i s_{i-1}   (s_i = B p_i)
+        x_{i+1} = x_i + alpha_i p_i,     r_{i+1} = r_i - alpha_i s_i
+        w_{i+1} = B r_{i+1},  gamma_{i+1} = (r_{i+1}, r_{i+1}),  delta_{i+1} = (w_{i+1}, r_{i+1})
+        beta_{i+1} = gamma_{i+1} / gamma_i
+        alpha_{i+1} = gamma_{i+1} / (delta_{i+1} - beta_{i+1} gamma_{i+1} / alpha_i)
+
+    (B = I + dt A).  Same start and stopping rule as cg_implicit_euler: x0 = b
+    when None; stop as soon as ||r_i||_2 <= rtol ||b||_2 (sqrt(gamma_i)), when
+    gamma_i == 0, or after maxit iterations.  Returns (x, iters)."""
+    b = np.asarray(b, dtype=np.float64)
+    x = np.array(b if x0 is None else x0, dtype=np.float64, copy=True)
+
+    def op(v):
+        return v + dt * apply_A(v, h, kappa)
+
+    bnorm = np.sqrt(np.sum(b * b))
+    r = b - op(x)
+    gamma = np.sum(r * r)
+    it = 0
+    if np.sqrt(gamma) <= rtol * bnorm or gamma == 0.0:
+        return x, it
+    w = op(r)
+    delta = np.sum(w * r)
+    alpha = gamma / delta
+    beta = 0.0
+    p = np.zeros_like(x)
+    s = np.zeros_like(x)
+    while it < maxit:
+        p = r + beta * p
+        s = w + beta * s
+        x = x + alpha * p
+        r = r - alpha * s
+        it += 1
+        gamma_new = np.sum(r * r)
+        if np.sqrt(gamma_new) <= rtol * bnorm or gamma_new == 0.0:
+            break
+        w = op(r)
+        delta = np.sum(w * r)
+        beta = gamma_new / gamma
+        alpha = gamma_new / (delta - beta * gamma_new / alpha)
+        gamma = gamma_new
+    return x, it
+
+
 def coarse_spectrum_bounds(n, h, dt: float, kappa=None):
     """Interval [a, b] holding the spectrum of I + dt A.
 
@@ -297,7 +350,9 @@ class Propagators:
     'implicit' (1D) or 'cn', the trapezoidal rule), f_rtol/f_maxit (CG of the
     trapezoidal steps in 2D/3D), g_solver ('thomas' or 'cg'), g_steps
     (default 1), g_rtol, g_maxit, g_cheb (0: plain CG; m >= 2: CG preconditioned
-    by m Chebyshev steps), kappa.  The coarse step is dT = f_steps * dt.
+    by m Chebyshev steps), g_cg ('textbook', default, or 'single': the
+    single-reduction recurrence of cg1_implicit_euler), kappa.  The coarse step
+    is dT = f_steps * dt.
     """
 
     def __init__(self, prob: dict, kappa="from_prob"):
@@ -312,6 +367,9 @@ class Propagators:
         self.g_rtol = float(prob.get("g_rtol", 1e-10))
         self.g_maxit = int(prob.get("g_maxit", 20000))
         self.g_cheb = int(prob.get("g_cheb") or 0)
+        self.g_cg = prob.get("g_cg") or "textbook"
+        if self.g_cg not in ("textbook", "single"):
+            raise ValueError("g_cg must be 'textbook' or 'single'")
         self.f_rtol = float(prob.get("f_rtol") or 1e-12)
         self.f_maxit = int(prob.get("f_maxit") or 10000)
         self.kappa = prob.get("kappa") if isinstance(kappa, str) else kappa
@@ -345,4 +403,6 @@ class Propagators:
         if self.g_cheb:
             return pcg_implicit_euler(x, dTg, self.h, self.kappa, x0, self.g_rtol, self.g_maxit,
                                       self.g_cheb)
+        if self.g_cg == "single":
+            return cg1_implicit_euler(x, dTg, self.h, self.kappa, x0, self.g_rtol, self.g_maxit)
         return cg_implicit_euler(x, dTg, self.h, self.kappa, x0, self.g_rtol, self.g_maxit)

@@ -258,6 +258,98 @@ def test_cg_matches_the_sine_transform_solution(n):
     assert it > 10
 
 
+@pytest.mark.parametrize("n", [(40, 33), (12, 10, 9)])
+def test_single_reduction_cg_matches_the_sine_transform_solution(n):
+    """The single-reduction (Chronopoulos-Gear) CG of the coarse step meets the
+    exact backward-Euler step DST^-1[DST(b) / (1 + dT mu)] at rtol 1e-14."""
+    h = tuple(1.0 / (m + 1) for m in n)
+    shape = tuple(reversed(n))
+    rng = np.random.default_rng(31)
+    b = rng.standard_normal(shape)
+    dT = 60 * min(h) ** 2
+    mu = grid_mu(n, h)
+    exact = scipy.fft.idstn(scipy.fft.dstn(b, type=1) / (1 + dT * mu), type=1)
+    x, it = heat.cg1_implicit_euler(b, dT, h, None, None, rtol=1e-14, maxit=2000)
+    assert np.linalg.norm(x - exact) / np.linalg.norm(exact) < 1e-12
+    assert it > 10
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_single_reduction_cg_dense_solve_and_mode(dim):
+    """Variable kappa: the dense solve (LAPACK) of I + dT A; constant kappa: a sine
+    mode comes out divided by 1 + dT mu."""
+    n = (5, 4) if dim == 2 else (3, 4, 3)
+    h = tuple(1.0 / (m + 1) for m in n)
+    shape = tuple(reversed(n))
+    rng = np.random.default_rng(32)
+    kap = np.exp(0.5 * rng.standard_normal(tuple(m + 2 for m in shape)))
+    b = rng.standard_normal(shape)
+    dT = 40 * min(h) ** 2
+    x, it = heat.cg1_implicit_euler(b, dT, h, kap, None, rtol=1e-14, maxit=500)
+    D = dense_of(lambda v: v + dT * heat.apply_A(v, h, kap), shape)
+    np.testing.assert_allclose(x.reshape(-1), np.linalg.solve(D, b.reshape(-1)), rtol=1e-11,
+                               atol=1e-12)
+    assert 0 < it <= D.shape[0] + 5
+    u = sine_mode(n, (2,) * dim, h)
+    mu = sum(4.0 / hh ** 2 * math.sin(2 * math.pi * hh / 2) ** 2 for hh in h)
+    xm, _ = heat.cg1_implicit_euler(u, dT, h, None, None, rtol=1e-14)
+    np.testing.assert_allclose(xm, u / (1 + dT * mu), rtol=1e-12, atol=1e-14)
+    # an eigenvector: one step of the Krylov method is exact (to rounding)
+    _, itm = heat.cg1_implicit_euler(u, dT, h, None, None, rtol=1e-10)
+    assert itm == 1
+
+
+def test_single_reduction_cg_has_the_krylov_iterates_of_textbook_cg():
+    """In exact arithmetic the single-reduction recurrence produces the iterates
+    of Hestenes-Stiefel CG (both minimise the B-norm error over the same Krylov
+    space).  Brute force on a small dense system: after j iterations both equal
+    the B-norm minimiser over x0 + K_j(B, r0), computed here by a dense
+    least-squares solve on an orthonormal Krylov basis (an independent route)."""
+    n = (6, 5)
+    h = tuple(1.0 / (m + 1) for m in n)
+    shape = tuple(reversed(n))
+    rng = np.random.default_rng(33)
+    kap = np.exp(0.4 * rng.standard_normal(tuple(m + 2 for m in shape)))
+    b = rng.standard_normal(shape)
+    x0 = rng.standard_normal(shape)
+    dT = 30 * min(h) ** 2
+    D = dense_of(lambda v: v + dT * heat.apply_A(v, h, kap), shape)
+    bb, xx0 = b.reshape(-1), x0.reshape(-1)
+    r0 = bb - D @ xx0
+    xstar = np.linalg.solve(D, bb)
+    L = np.linalg.cholesky(D)
+    for j in range(1, 7):
+        K = np.stack([np.linalg.matrix_power(D, i) @ r0 for i in range(j)], axis=1)
+        Q, _ = np.linalg.qr(K)
+        # min over c of ||L^T (x0 + Q c - x*)||_2
+        c, *_ = np.linalg.lstsq(L.T @ Q, L.T @ (xstar - xx0), rcond=None)
+        xj = xx0 + Q @ c
+        x1, it1 = heat.cg1_implicit_euler(b, dT, h, kap, x0, rtol=0.0, maxit=j)
+        xt, itt = heat.cg_implicit_euler(b, dT, h, kap, x0, rtol=0.0, maxit=j)
+        assert it1 == itt == j
+        assert np.linalg.norm(x1.reshape(-1) - xj) / np.linalg.norm(xj) < 1e-9, j
+        assert np.linalg.norm(xt.reshape(-1) - xj) / np.linalg.norm(xj) < 1e-9, j
+
+
+def test_single_reduction_cg_zero_rhs_warm_start_and_stop_rule():
+    h = (1 / 6, 1 / 6)
+    x, it = heat.cg1_implicit_euler(np.zeros((5, 5)), 0.1, h)
+    assert it == 0 and not x.any()
+    b = np.random.default_rng(34).standard_normal((5, 5))
+    xs, _ = heat.cg1_implicit_euler(b, 0.1, h, rtol=1e-14)
+    x2, it2 = heat.cg1_implicit_euler(b, 0.1, h, x0=xs, rtol=1e-10)
+    assert it2 == 0
+    # the stop rule is on the recursively updated residual against rtol ||b||_2,
+    # as for textbook CG: same iteration count on a mid-size grid
+    n = (40, 33)
+    hh = tuple(1.0 / (m + 1) for m in n)
+    bb = np.random.default_rng(35).standard_normal(tuple(reversed(n)))
+    for rtol in (1e-4, 1e-7, 1e-10):
+        _, i1 = heat.cg1_implicit_euler(bb, 60 * min(hh) ** 2, hh, None, None, rtol, 2000)
+        _, i0 = heat.cg_implicit_euler(bb, 60 * min(hh) ** 2, hh, None, None, rtol, 2000)
+        assert abs(i1 - i0) <= 1, (rtol, i1, i0)
+
+
 @pytest.mark.parametrize("m", [2, 5, 8])
 def test_chebyshev_preconditioner_on_a_mode(m):
     """On an eigenvector of B = I + dT A with eigenvalue lam, m Chebyshev steps give
