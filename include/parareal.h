@@ -261,11 +261,24 @@ int parareal_adjoint_async(pr_ctx* ctx, const pr_event* log_host, size_t n_event
  *    I + dT A >= I, lies within 2 g_rtol ||b||_2 of the plain CG result).
  *    Needs M doubles and 4 M floats more.  The asynchronous kernel keeps plain
  *    CG. */
+/* and one that changes the coarse CG's recurrence (not its iterates in exact
+ * arithmetic, nor its stopping rule):
+ *  PR_OPT_G_CG (0 = automatic, default; 1 = textbook; 2 = single-reduction):
+ *    the unpreconditioned coarse CG of the synchronous driver, the predictor,
+ *    parareal_coarse and the adjoint runs either textbook (Hestenes-Stiefel)
+ *    CG, three device-wide barriers and two reductions per iteration, or the
+ *    single-reduction recurrence of Chronopoulos and Gear, whose two inner
+ *    products r.r and (B r).r are reduced together: two barriers and one
+ *    reduction per iteration for one more vector update per point.  Automatic
+ *    picks single-reduction for grids of at most 2^21 points (their vectors
+ *    stay in L2 and the barriers dominate an iteration) and textbook above.
+ *    The iterates agree to rounding; the iteration counts to about one. */
 enum pr_option {
   PR_OPT_PIPELINE = 1,
   PR_OPT_PIPELINE_CHUNKS = 2,
   PR_OPT_CG_BLOCKS_PER_SM = 3,
-  PR_OPT_G_CHEBYSHEV = 4
+  PR_OPT_G_CHEBYSHEV = 4,
+  PR_OPT_G_CG = 5
 };
 int parareal_set_option(pr_ctx* ctx, int option, double value);
 
@@ -299,6 +312,18 @@ int parareal_slice_stats(pr_ctx* ctx, int* k_host, double* delta_host);
 int parareal_coarse_noalloc(int dim, const int* n, double dT, const double* b_dev,
                             const double* x0_dev, double* x_dev, double rtol, int maxit,
                             int* iters_host, void* cuda_stream);
+
+/* FP64-pipe throughput probe (a measurement aid; the paper has no
+ * counterpart): runs 4 blocks of 256 threads per SM on the current device,
+ * each thread executing `iters` rounds of eight independent FP64 operations
+ * (kind 0: DFMA x = x a + b; kind 1: DADD x = x + b), once untimed and once
+ * timed with CUDA events on the given stream (synchronised before return).
+ * *ops_per_s_host receives FP64 instructions per second of the timed launch,
+ * *ops_host (may be NULL) the instruction count.  scratch_dev: one device
+ * double, written only if the chains overflow (never for iters <= 2^32).
+ * PR_EINVAL for a kind other than 0/1 or iters outside [1, 2^32]. */
+int parareal_probe_fp64(int kind, long long iters, double* scratch_dev, double* ops_per_s_host,
+                        long long* ops_host, void* cuda_stream);
 
 void parareal_destroy(pr_ctx* ctx);
 const char* parareal_last_error(const pr_ctx* ctx);

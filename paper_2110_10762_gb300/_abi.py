@@ -17,6 +17,7 @@ STATUS_NAMES = {0: "PR_OK", 1: "PR_EINVAL", 2: "PR_ENOMEM", 3: "PR_ECUDA", 4: "P
 PR_EXPLICIT_EULER, PR_IMPLICIT_EULER, PR_CRANK_NICOLSON = 0, 1, 2
 PR_SOLVER_THOMAS, PR_SOLVER_CG = 0, 1
 PR_OPT_PIPELINE, PR_OPT_PIPELINE_CHUNKS, PR_OPT_CG_BLOCKS_PER_SM, PR_OPT_G_CHEBYSHEV = 1, 2, 3, 4
+PR_OPT_G_CG = 5
 
 
 class pr_problem(C.Structure):
@@ -76,6 +77,8 @@ EXPORTS = {
     "parareal_coarse_noalloc": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.c_double, C.c_void_p,
                                           C.c_void_p, C.c_void_p, C.c_double, C.c_int,
                                           C.POINTER(C.c_int), C.c_void_p]),
+    "parareal_probe_fp64": (C.c_int, [C.c_int, C.c_longlong, C.c_void_p, C.POINTER(C.c_double),
+                                      C.POINTER(C.c_longlong), C.c_void_p]),
     "parareal_destroy": (None, [C.c_void_p]),
     "parareal_last_error": (C.c_char_p, [C.c_void_p]),
     "parareal_version": (C.c_char_p, []),

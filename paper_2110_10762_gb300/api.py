@@ -237,6 +237,23 @@ def parareal_coarse_noalloc(dim: int, n, dT: float, b, x0, x_out, rtol: float = 
     return it.value
 
 
+def parareal_probe_fp64(kind: int, iters: int = 1 << 16, stream=None):
+    """FP64-pipe throughput of the current device (kind 0: DFMA, 1: DADD), in
+    FP64 instructions per second; see include/parareal.h.  Returns (rate, count)."""
+    import torch
+    scratch = torch.zeros(1, dtype=torch.float64, device="cuda")
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    if not isinstance(stream, int):
+        stream = stream.cuda_stream
+    rate, ops = C.c_double(0.0), C.c_longlong(0)
+    code = _lib().parareal_probe_fp64(int(kind), int(iters), _ptr(scratch), C.byref(rate),
+                                      C.byref(ops), stream)
+    if code != PR_OK:
+        raise PararealError(code, "parareal_probe_fp64 failed")
+    return rate.value, ops.value
+
+
 def parareal_destroy(ctx):
     if ctx:
         _lib().parareal_destroy(ctx)

@@ -41,7 +41,7 @@ bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 void free_problem(pr_ctx* c) {
   void* ptrs[] = {c->fcoef, c->fcoef32, c->gcoef, c->fsys0, c->v, c->w, c->tmp, c->f32a, c->f32b,
                   c->tma_err,
-                  c->cg_x, c->cg_r, c->cg_p, c->cg_q, c->cg_part, c->cg_iters_dev,
+                  c->cg_x, c->cg_r, c->cg_p, c->cg_q, c->cg_w, c->cg_part, c->cg_iters_dev,
                   c->delta_dev, c->u0_stage, c->lam_stage, c->async_ws, c->adj_ws};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -53,7 +53,7 @@ void free_problem(pr_ctx* c) {
   c->f32a = c->f32b = nullptr;
   c->tma_err = nullptr;
   c->tma_ok = false;
-  c->cg_x = c->cg_r = c->cg_p = c->cg_q = c->cg_part = nullptr;
+  c->cg_x = c->cg_r = c->cg_p = c->cg_q = c->cg_w = c->cg_part = nullptr;
   c->cg_iters_dev = nullptr;
   c->delta_dev = nullptr;
   c->u0_stage = c->lam_stage = nullptr;
@@ -271,6 +271,7 @@ int parareal_set_problem(pr_ctx* c, const pr_problem* pin) {
   alloc(&c->cg_r, g.M);
   alloc(&c->cg_p, g.M);
   alloc(&c->cg_q, g.M);
+  alloc(&c->cg_w, g.M);
   alloc(&c->cg_part, 6 * (size_t)c->cg_blocks);
   alloc(&c->cg_iters_dev, (size_t)p.N + 1);
   alloc(&c->delta_dev, (size_t)p.N);
@@ -444,6 +445,11 @@ int parareal_set_option(pr_ctx* c, int option, double value) {
           return cuda_fail(c, e, "Chebyshev workspaces");
         }
       }
+      return PR_OK;
+    case PR_OPT_G_CG:
+      if (!(value == 0.0 || value == 1.0 || value == 2.0))
+        return fail(c, PR_EINVAL, "coarse CG recurrence must be 0, 1 or 2");
+      c->opt_g_cg = (int)value;
       return PR_OK;
     default:
       return fail(c, PR_EINVAL, "unknown option");

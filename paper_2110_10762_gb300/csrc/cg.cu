@@ -1,5 +1,7 @@
 // Coarse propagator G: one backward-Euler step (I + dT A) x = b (§5.1),
-// solved by textbook (Hestenes-Stiefel) conjugate gradients in FP64 as one
+// solved by conjugate gradients in FP64 -- textbook (Hestenes-Stiefel) or the
+// single-reduction recurrence of Chronopoulos and Gear, which has the same
+// iterates -- as one
 // cooperative persistent kernel: every block owns a grid-stride share of the
 // points, dot products are warp-shuffle + block reductions followed by one
 // grid barrier and a fixed-order sum of the block partials (deterministic:
@@ -283,15 +285,22 @@ __device__ int pcg_core(const CgDev& a, int nblk, int blk) {
 // partials and barrier arrivals); beyond that the phases stream from HBM and
 // are latency-bound, so a 4-blocks/SM instance (<= 64 registers) keeps twice
 // as many loads in flight (measured 707 -> ~550 us per iteration at 256^3).
-template <int MINB, bool PCG>
+// ALG: CG_TEXTBOOK, CG_SINGLE (single-reduction recurrence) or CG_CHEB
+// (Chebyshev-preconditioned).
+enum { CG_TEXTBOOK = 0, CG_SINGLE = 1, CG_CHEB = 2 };
+
+template <int MINB, int ALG>
 __global__ void __launch_bounds__(CG_THREADS, MINB) cg_kernel(CgDev a) {
   const long long M = a.g.M;
   const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long nt = (long long)gridDim.x * blockDim.x;
   if (a.mode == CG_CORRECT && t0 == 0) *a.delta = 0ull;
   int it;
-  if constexpr (PCG)
+  if constexpr (ALG == CG_CHEB)
     it = pcg_core(a, gridDim.x, blockIdx.x);
+  else if constexpr (ALG == CG_SINGLE)
+    it = cg1_core(a.g, a.k, a.var != 0, a.gv, a.b, a.x0, a.rtol, a.maxit, a.ws, GridBarrier{},
+                  gridDim.x, blockIdx.x);
   else
     it = cg_core(a.g, a.k, a.var != 0, a.gv, a.b, a.x0, a.rtol, a.maxit, a.ws, GridBarrier{},
                  gridDim.x, blockIdx.x);
@@ -349,10 +358,10 @@ constexpr long long CG_L2_POINTS = 2LL << 20;  // 5 FP64 vectors of 2 M points =
 #endif
 constexpr int CG_BIG = PR_CG_BIG_MINB;  // blocks per SM of the instance for grids beyond L2
 
-template <int MINB, bool PCG = false>
+template <int MINB, int ALG = CG_TEXTBOOK>
 int cg_blocks_of(int num_sms) {
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_kernel<MINB, PCG>, CG_THREADS, 0) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_kernel<MINB, ALG>, CG_THREADS, 0) !=
           cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
@@ -360,12 +369,16 @@ int cg_blocks_of(int num_sms) {
   return per_sm * num_sms;
 }
 
+template <int ALG>
+int cg_blocks_any(int num_sms) {
+  return std::max(cg_blocks_of<2, ALG>(num_sms), cg_blocks_of<CG_BIG, ALG>(num_sms));
+}
+
 }  // namespace
 
 int cg_max_blocks(int num_sms) {
-  const int a = std::max(cg_blocks_of<2>(num_sms), cg_blocks_of<CG_BIG>(num_sms));
-  const int b = std::max(cg_blocks_of<2, true>(num_sms), cg_blocks_of<CG_BIG, true>(num_sms));
-  return a > b ? a : b;
+  return std::max(cg_blocks_any<CG_TEXTBOOK>(num_sms),
+                  std::max(cg_blocks_any<CG_SINGLE>(num_sms), cg_blocks_any<CG_CHEB>(num_sms)));
 }
 
 cudaError_t cg_solve(pr_ctx* c, const CgArgs& in) {
@@ -382,7 +395,7 @@ cudaError_t cg_solve(pr_ctx* c, const CgArgs& in) {
   a.delta = in.delta;
   a.iters = in.iters;
   a.mode = in.mode;
-  a.ws = {c->cg_x, c->cg_r, c->cg_p, c->cg_q, c->cg_part};
+  a.ws = {c->cg_x, c->cg_r, c->cg_p, c->cg_q, c->cg_part, c->cg_w};
   a.rtol = c->prob.g_rtol;
   a.maxit = c->prob.g_maxit;
   if (c->opt_g_cheb >= 2 && c->cheb_z) {
@@ -413,9 +426,24 @@ cudaError_t cg_solve(pr_ctx* c, const CgArgs& in) {
     ch.d1 = ch.d0 + c->g.M;
   }
   const bool big = c->g.M > CG_L2_POINTS;
-  const bool pcg = a.ch.m >= 2;
-  int cap = big ? (pcg ? cg_blocks_of<CG_BIG, true>(c->num_sms) : cg_blocks_of<CG_BIG>(c->num_sms))
-                : (pcg ? cg_blocks_of<2, true>(c->num_sms) : cg_blocks_of<2>(c->num_sms));
+  // recurrence: preconditioned, or single-reduction where the barriers dominate
+  // an iteration (vectors resident in L2), textbook otherwise (PR_OPT_G_CG)
+  const int alg = a.ch.m >= 2 ? CG_CHEB
+                  : c->opt_g_cg == 2 ? CG_SINGLE
+                  : c->opt_g_cg == 1 ? CG_TEXTBOOK
+                  : big ? CG_TEXTBOOK : CG_SINGLE;
+  int cap = 0;
+  void* fn = nullptr;
+  if (alg == CG_CHEB) {
+    cap = big ? cg_blocks_of<CG_BIG, CG_CHEB>(c->num_sms) : cg_blocks_of<2, CG_CHEB>(c->num_sms);
+    fn = big ? (void*)cg_kernel<CG_BIG, CG_CHEB> : (void*)cg_kernel<2, CG_CHEB>;
+  } else if (alg == CG_SINGLE) {
+    cap = big ? cg_blocks_of<CG_BIG, CG_SINGLE>(c->num_sms) : cg_blocks_of<2, CG_SINGLE>(c->num_sms);
+    fn = big ? (void*)cg_kernel<CG_BIG, CG_SINGLE> : (void*)cg_kernel<2, CG_SINGLE>;
+  } else {
+    cap = big ? cg_blocks_of<CG_BIG>(c->num_sms) : cg_blocks_of<2>(c->num_sms);
+    fn = big ? (void*)cg_kernel<CG_BIG, CG_TEXTBOOK> : (void*)cg_kernel<2, CG_TEXTBOOK>;
+  }
   // a caller-chosen blocks-per-SM cap leaves room for concurrent kernels
   if (c->opt_cg_bps > 0 && c->opt_cg_bps * c->num_sms < cap) cap = c->opt_cg_bps * c->num_sms;
   long long want = (c->g.M + CG_THREADS * 4 - 1) / (CG_THREADS * 4);
@@ -423,8 +451,6 @@ cudaError_t cg_solve(pr_ctx* c, const CgArgs& in) {
   if (blocks > c->cg_blocks) blocks = c->cg_blocks;  // partials are sized for cg_blocks
   if (blocks < 1) blocks = 1;
   void* args[] = {&a};
-  void* fn = big ? (pcg ? (void*)cg_kernel<CG_BIG, true> : (void*)cg_kernel<CG_BIG, false>)
-                 : (pcg ? (void*)cg_kernel<2, true> : (void*)cg_kernel<2, false>);
   return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(CG_THREADS), args, 0, c->stream);
 }
 

@@ -98,6 +98,7 @@ struct pr_ctx {
   double* cg_r = nullptr;
   double* cg_p = nullptr;
   double* cg_q = nullptr;
+  double* cg_w = nullptr;    // single-reduction CG: B r (M)
   double* cg_part = nullptr; // per-block partial sums (2 parities x 3 values x cg_blocks)
   int* cg_iters_dev = nullptr;   // per slot CG iteration counts (N+1)
   unsigned long long* delta_dev = nullptr;  // per slice increments (N), bits of non-negative doubles
@@ -114,6 +115,7 @@ struct pr_ctx {
   int opt_chunks = 8;        // slice chunks per pipelined fine batch
   int opt_cg_bps = 0;        // CG blocks per SM (0 = automatic)
   int opt_g_cheb = 0;        // Chebyshev steps of the coarse CG preconditioner (0 = plain CG)
+  int opt_g_cg = 0;          // coarse CG recurrence: 0 automatic, 1 textbook, 2 single-reduction
   double g_lo = 0, g_hi = 0; // spectrum bounds of I + dT A
   double* cheb_z = nullptr;  // preconditioned residual (M)
   float* cheb_f32 = nullptr; // FP32 Chebyshev vectors (4 M)

@@ -284,8 +284,9 @@ struct CgWork {
   double* x;
   double* r;
   double* p;
-  double* q;
+  double* q;     // textbook: q = B p; single-reduction: s = B p (by recurrence)
   double* part;  // 2 parity buffers x 3 values x nblk
+  double* w;     // single-reduction CG only: w = B r
 };
 
 #ifndef PR_CG_FAST
@@ -396,6 +397,188 @@ __device__ __forceinline__ void cg_update_p(double* __restrict__ p, const double
     p[j] = pj;
   }
   if (i < M) p[i] = fma(beta, p[i], r[i]);
+}
+
+// w = B r on this block's rows with the partial products r.r and w.r (the two
+// inner products of the single-reduction CG), two warp-rows per trip.
+__device__ __forceinline__ void cg1_matvec_dots(const Geom& g, const StencilConst& k, bool var,
+                                                bool scaled, const StencilVar<double>& gv,
+                                                const double* __restrict__ r,
+                                                double* __restrict__ w, int blk, int nblk,
+                                                double& rr, double& wr) {
+  const int lane = threadIdx.x & 31;
+  double ga = 0.0, gb = 0.0, da = 0.0, db = 0.0;
+  RowIter ra(g, blk, nblk), rb(g, blk, nblk);
+  rb.advance();
+  while (ra.z < g.nz) {
+    const int xa = ra.seg * 32 + lane;
+    const int xb = rb.seg * 32 + lane;
+    const bool oka = xa < g.nx;
+    const bool okb = rb.z < g.nz && xb < g.nx;
+    const long long ia = ((long long)ra.z * g.ny + ra.y) * g.nx + xa;
+    const long long ib = ((long long)rb.z * g.ny + rb.y) * g.nx + xb;
+    double wa = 0.0, wb = 0.0;
+    if (oka) wa = op_point(g, k, var, scaled, gv, r, xa, ra.y, ra.z, ia);
+    if (okb) wb = op_point(g, k, var, scaled, gv, r, xb, rb.y, rb.z, ib);
+    if (oka) {
+      const double rv = r[ia];
+      w[ia] = wa;
+      ga = fma(rv, rv, ga);
+      da = fma(wa, rv, da);
+    }
+    if (okb) {
+      const double rv = r[ib];
+      w[ib] = wb;
+      gb = fma(rv, rv, gb);
+      db = fma(wb, rv, db);
+    }
+    ra.advance();
+    ra.advance();
+    rb.advance();
+    rb.advance();
+  }
+  rr = ga + gb;
+  wr = da + db;
+}
+
+// Direction and solution updates of the single-reduction CG over this block's
+// share: p = r + beta p, s = w + beta s (s = B p), x += ax p, r -= ar s.  On the
+// first iteration (first = true) p = r and s = w without reading p and s.
+__device__ __forceinline__ void cg1_update(const CgWork& ws, double beta, double ax, double ar,
+                                           bool first, long long t0, long long nt, long long M) {
+  double* __restrict__ x = ws.x;
+  double* __restrict__ r = ws.r;
+  double* __restrict__ p = ws.p;
+  double* __restrict__ s = ws.q;
+  const double* __restrict__ w = ws.w;
+  if (first) {
+    for (long long i = t0; i < M; i += nt) {
+      const double ri = r[i], wi = w[i];
+      p[i] = ri;
+      s[i] = wi;
+      x[i] = fma(ax, ri, x[i]);
+      r[i] = fma(-ar, wi, ri);
+    }
+    return;
+  }
+  long long i = t0;
+  for (; i + nt < M; i += 2 * nt) {
+    const long long j = i + nt;
+    const double ri = r[i], rj = r[j];
+    const double pi = fma(beta, p[i], ri);
+    const double pj = fma(beta, p[j], rj);
+    const double si = fma(beta, s[i], w[i]);
+    const double sj = fma(beta, s[j], w[j]);
+    p[i] = pi;
+    p[j] = pj;
+    s[i] = si;
+    s[j] = sj;
+    x[i] = fma(ax, pi, x[i]);
+    x[j] = fma(ax, pj, x[j]);
+    r[i] = fma(-ar, si, ri);
+    r[j] = fma(-ar, sj, rj);
+  }
+  if (i < M) {
+    const double ri = r[i];
+    const double pi = fma(beta, p[i], ri);
+    const double si = fma(beta, s[i], w[i]);
+    p[i] = pi;
+    s[i] = si;
+    x[i] = fma(ax, pi, x[i]);
+    r[i] = fma(-ar, si, ri);
+  }
+}
+
+// Single-reduction CG (Chronopoulos and Gear) for (I + dT A) x = b over a group
+// of `nblk` blocks: the Krylov iterates of textbook CG with both inner products
+// of an iteration, r.r and (B r).r, reduced together, so an iteration takes two
+// group barriers (after the update of r, whose neighbours the operator reads;
+// after the partial sums) instead of three, and one reduction instead of two:
+//   p = r + beta p,  s = w + beta s,  x += alpha p,  r -= alpha s;
+//   w = B r,  gamma' = r.r,  delta = w.r;
+//   beta = gamma' / gamma,  alpha = gamma' / (delta - beta gamma' / alpha).
+// Start, stopping rule (||r||_2 <= rtol ||b||_2 on the recursively updated
+// residual, r == 0, or maxit) and return value as cg_core.  Needs ws.w.
+template <class Barrier>
+__device__ int cg1_core(const Geom& g, const StencilConst& k, bool var,
+                        const StencilVar<double>& gv, const double* __restrict__ b,
+                        const double* __restrict__ x0, double rtol, int maxit, const CgWork& ws,
+                        const Barrier& bar, int nblk, int blk) {
+  const long long M = g.M;
+  const long long t0 = blk * (long long)blockDim.x + threadIdx.x;
+  const long long nt = (long long)nblk * blockDim.x;
+  int parity = 0;
+  auto part = [&]() { return ws.part + (size_t)parity * 3 * nblk; };
+  double s_rr = 0.0, s_bb = 0.0;
+  for_each_point(g, blk, nblk, [&](int x, int y, int z, long long i) {
+    const double bi = b[i];
+    const double ri = bi - gop_xyz(g, k, var, gv, x0, x, y, z, i);
+    ws.x[i] = x0[i];
+    ws.r[i] = ri;
+    s_rr += ri * ri;
+    s_bb += bi * bi;
+  });
+  {
+    const double v[2] = {s_rr, s_bb};
+    block_sum<2>(v, part(), blk);
+  }
+  if (!bar.sync()) return -1;
+  // threshold, stop flag and the operator scaled by 1/R_x (constant kappa):
+  // w' = w / R_x, s' = s / R_x, delta' = delta / R_x, alpha' = R_x alpha;
+  // r -= alpha' s', x += (alpha' / R_x) p
+  double o8[8];
+  group_sum<2, 8>(part(), nblk, o8, [&](double* r) {
+    r[2] = rtol * sqrt(r[1]);
+    r[3] = (sqrt(r[0]) <= r[2] || r[0] == 0.0 || maxit <= 0) ? 1.0 : 0.0;
+    r[4] = k.c0 / k.rx;
+    r[5] = k.ry / k.rx;
+    r[6] = k.rz / k.rx;
+    r[7] = 1.0 / k.rx;
+  });
+  parity ^= 1;
+  if (o8[3] != 0.0) return 0;
+  double gamma = o8[0];
+  const double thresh = o8[2];
+  const bool scaled = !var;
+  const StencilConst ks = scaled ? StencilConst{o8[4], 1.0, o8[5], o8[6]} : k;
+  const double sc = scaled ? o8[7] : 1.0;
+  {
+    double rr, wr;
+    cg1_matvec_dots(g, ks, var, scaled, gv, ws.r, ws.w, blk, nblk, rr, wr);
+    const double v[1] = {wr};
+    block_sum<1>(v, part(), blk);
+  }
+  if (!bar.sync()) return -1;
+  double o2[2];
+  group_sum<1, 2>(part(), nblk, o2, [&](double* r) { r[1] = gamma / r[0]; });
+  parity ^= 1;
+  double alpha = o2[1], beta = 0.0;
+  int it = 0;
+  while (true) {
+    cg1_update(ws, beta, alpha * sc, alpha, it == 0, t0, nt, M);
+    if (!bar.sync()) return -1;
+    {
+      double rr, wr;
+      cg1_matvec_dots(g, ks, var, scaled, gv, ws.r, ws.w, blk, nblk, rr, wr);
+      const double v[2] = {rr, wr};
+      block_sum<2>(v, part(), blk);
+    }
+    if (!bar.sync()) return -1;
+    ++it;
+    double o5[5];
+    group_sum<2, 5>(part(), nblk, o5, [&](double* r) {
+      const double gn = r[0];
+      r[2] = (sqrt(gn) <= thresh || gn == 0.0 || it >= maxit) ? 1.0 : 0.0;
+      const double bt = gn / gamma;
+      r[3] = bt;
+      r[4] = gn / (r[1] - bt * gn / alpha);
+    });
+    parity ^= 1;
+    if (o5[2] != 0.0) return it;
+    gamma = o5[0];
+    beta = o5[3];
+    alpha = o5[4];
+  }
 }
 
 template <class Barrier>

@@ -148,6 +148,66 @@ def test_coarse_propagator(case):
         assert np.linalg.norm(r) <= 1e-12 * np.linalg.norm(b) * 10
 
 
+@pytest.mark.parametrize("case", ["2d_const", "2d_var", "3d_const", "3d_var", "1d_explicit"])
+@pytest.mark.parametrize("recurrence", ["textbook", "single"])
+def test_coarse_cg_recurrences_match_their_oracle(case, recurrence):
+    """PR_OPT_G_CG forces each coarse CG recurrence; each is compared with the
+    oracle's CG of the same recurrence (solution at 1e-12, iteration count within
+    2) from a warm start and from the right-hand side."""
+    p = CASES[case]()
+    p["g_cg"] = recurrence
+    rng = np.random.default_rng(17)
+    shape = tuple(reversed(p["n"]))
+    b = rng.standard_normal(shape)
+    P = oracle_props(p)
+    with Ctx(p) as c:
+        pr.parareal_set_option(c.ctx, pr.PR_OPT_G_CG, 1 if recurrence == "textbook" else 2)
+        for x0 in (b + 0.1 * rng.standard_normal(shape), None):
+            ref, ref_it = P.G(b, x0=x0)
+            out = torch().empty(c.M, dtype=torch().float64, device="cuda")
+            it = pr.parareal_coarse(c.ctx, dev(b), None if x0 is None else dev(x0), out)
+            got = host(out)
+            assert rel_l2(got, ref) < FP64_TOL
+            assert abs(it - ref_it) <= 2, (it, ref_it)
+
+
+def test_single_reduction_cg_on_an_hbm_resident_grid():
+    """The single-reduction recurrence forced on the 4-blocks/SM instance (2.5 M points)."""
+    n = (136, 136, 136)
+    rng = np.random.default_rng(18)
+    h = tuple(1.0 / (m + 1) for m in n)
+    shape = tuple(reversed(n))
+    p = dict(dim=3, n=n, h=h, N=1, f_steps=64, dt=0.15 * h[0] ** 2, f_scheme="explicit",
+             g_solver="cg", g_rtol=1e-8, u0=np.zeros(shape), tol=0.0, g_cg="single")
+    b = rng.standard_normal(shape)
+    ref, ref_it = oracle_props(p).G(b)
+    with Ctx(p) as c:
+        pr.parareal_set_option(c.ctx, pr.PR_OPT_G_CG, 2)
+        out = torch().empty(c.M, dtype=torch().float64, device="cuda")
+        it = pr.parareal_coarse(c.ctx, dev(b), None, out)
+        got = host(out)
+    assert abs(it - ref_it) <= 2
+    assert rel_l2(got, ref) < 1e-10
+
+
+@pytest.mark.parametrize("case", ["2d_const", "2d_var"])
+def test_sync_parareal_single_reduction_coarse_matches_oracle(case):
+    """Algorithm 1 with the single-reduction coarse CG on both sides (the GPU's
+    automatic choice on grids that fit in L2), every iterate."""
+    p = CASES[case]()
+    p["g_cg"] = "single"
+    ref = sync_parareal(p, tol=0.0, record=True)
+    with Ctx(p) as c:
+        pr.parareal_set_option(c.ctx, pr.PR_OPT_G_CG, 2)
+        for k in (1, 2, p["N"] // 2, p["N"]):
+            c.prob.max_iter = k
+            c.prob.tol = 0.0
+            pr.parareal_set_problem(c.ctx, c.prob)
+            lam = c.lam()
+            pr.parareal_run_sync(c.ctx, lam)
+            assert rel_l2(host(lam), ref.iterates[k]) < FP64_TOL, k
+
+
 def test_coarse_propagator_hbm_resident_grid():
     """2.5 M points (the CG instance sized for grids that do not fit in L2)."""
     n = (136, 136, 136)
