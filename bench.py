@@ -164,7 +164,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="heat2d_explicit", choices=list(WORKLOADS))
+    ap.add_argument("--workload", default="heat3d_mixed", choices=list(WORKLOADS))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
     ap.add_argument("--profile", action="store_true",
@@ -177,8 +177,12 @@ def parse():
     ap.add_argument("--pipeline", action="store_true",
                     help="overlap F of iteration k+1 with the coarse sweep of iteration k")
     ap.add_argument("--chunks", type=int, default=8, help="slice chunks per pipelined F batch")
-    ap.add_argument("--g-cheb", type=int, default=0,
-                    help="coarse CG preconditioned by this many FP32 Chebyshev steps (0 = plain CG)")
+    ap.add_argument("--g-cheb", type=int, default=None,
+                    help="coarse CG preconditioned by this many FP32 Chebyshev steps (0 = plain "
+                         "CG; default: the workload's setting)")
+    ap.add_argument("--g-cg", type=int, default=0, choices=[0, 1, 2],
+                    help="unpreconditioned coarse CG recurrence: 0 automatic, 1 textbook, "
+                         "2 single-reduction")
     ap.add_argument("--ctas-per-slice", type=int, default=0,
                     help="async workloads: CTAs per slice team (0 = automatic)")
     ap.add_argument("--lazy", action="store_true",
@@ -281,14 +285,38 @@ G_RTOL_OVERRIDE = None
 SIZE_OVERRIDE = {}
 
 
-def problem_of(name):
-    from synthetic import preset
+def preset_args(name):
+    """(preset name, overrides) of a workload: the synthetic recipe and the
+    size/tolerance overrides given on the command line."""
     base = {"heat2d_async": "heat2d_explicit", "heat2d_cn_async": "heat2d_cn",
             "heat2d_inverse_async": "heat2d_inverse"}.get(name, name)
-    p = preset(base, "full", **SIZE_OVERRIDE)
+    over = dict(SIZE_OVERRIDE)
     if G_RTOL_OVERRIDE is not None:
-        p["g_rtol"] = G_RTOL_OVERRIDE
-    return p
+        over["g_rtol"] = G_RTOL_OVERRIDE
+    return base, over
+
+
+def problem_of(name):
+    from synthetic import preset
+    base, over = preset_args(name)
+    return preset(base, "full", **over)
+
+
+def bench_config(args, p, world=1):
+    """`config` of the bench line; the reference arm prints the same keys."""
+    cfg = {"workload": WORKLOADS[args.workload], "grid": list(p["n"]), "N": p["N"],
+           "f_steps": p["f_steps"], "tol": p.get("tol"), "g_rtol": p.get("g_rtol"),
+           "f_prec": p.get("f_prec", 64),
+           "parallelism": "replicas" if world > 1 else "1 GPU",
+           "schedule": ("pipelined (F of k+1 overlaps the sweep of k)"
+                        if getattr(args, "pipeline", False) else "plain"),
+           "coarse_solver": ("Thomas (partition tridiagonal solver)"
+                             if p.get("g_solver") == "thomas" else
+                             "CG preconditioned by %d FP32 Chebyshev steps" % args.g_cheb
+                             if args.g_cheb else "CG"),
+           "l2": "inputs larger than L2 (trajectory %.2f GB + workspaces)" % (
+               (p["N"] + 1) * math.prod(p["n"]) * 8 / 1e9)}
+    return cfg
 
 
 def problem_struct(pr, p, u0, kappa=None, **over):
@@ -305,77 +333,212 @@ def problem_struct(pr, p, u0, kappa=None, **over):
     return pr.make_problem(**kw)
 
 
-def cpu_sample(p, slices=2, steps=None):
-    """The FP64 oracle's fine propagator on a bounded sample of the workload."""
-    import numpy as np
+# ---------------------------------------------------------------- CPU baseline
+# The FP64 oracle (numpy, as it stands) timed on all host cores: a pool of
+# spawned processes, one slice per process (the slices' fine propagations are
+# independent, Algorithm 1), each single-threaded.  Spawned, not forked: a
+# child forked after the first CUDA call can hang.
+_ORACLE = {}
+
+
+def _oracle_init(name, over):
     from oracle import heat
-    steps = p["f_steps"] if steps is None else steps
+    from synthetic import preset
+    _ORACLE["p"] = preset(name, "full", **over)
+    _ORACLE["heat"] = heat
+
+
+def _oracle_fine_task(args):
+    """One slice's F, `steps` fine steps of the full grid; returns (LUPs, t0, t1)."""
+    import numpy as np
+    seed, steps = args
+    p, heat = _ORACLE["p"], _ORACLE["heat"]
     P = heat.Propagators(dict(p, f_steps=steps))
-    rng = np.random.default_rng(0)
+    x = p["u0"] + 0.01 * np.random.default_rng(seed).standard_normal(p["u0"].shape)
+    t0 = time.time()
+    P.F(x)
+    t1 = time.time()
+    return steps * int(np.prod(p["n"])), t0, t1
+
+
+def _oracle_cg_task(iters):
+    """`iters` iterations of the oracle's coarse CG on the full grid; returns seconds."""
+    p, heat = _ORACLE["p"], _ORACLE["heat"]
+    P = heat.Propagators(dict(p, g_rtol=0.0, g_maxit=iters))
     t0 = time.perf_counter()
-    for _ in range(slices):
-        P.F(p["u0"] + 0.01 * rng.standard_normal(p["u0"].shape))
-    dt = time.perf_counter() - t0
-    lups = slices * steps * int(np.prod(p["n"]))
-    return lups / dt / 1e9, dt, lups
+    P.G(p["u0"])
+    return time.perf_counter() - t0
+
+
+class OraclePool:
+    """All host cores running the oracle, one slice per spawned process."""
+
+    def __init__(self, name, over, cores=None):
+        import multiprocessing as mp
+        self.cores = cores or os.cpu_count() or 1
+        os.environ.setdefault("OMP_NUM_THREADS", "1")
+        os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+        self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_oracle_init,
+                                                 initargs=(name, dict(over)))
+
+    def fine(self, steps):
+        """Every core propagates one slice by `steps` fine steps at once; returns
+        (GLUP/s over the wall time of the parallel region, seconds, LUPs)."""
+        res = self.pool.map(_oracle_fine_task, [(s, steps) for s in range(self.cores)],
+                            chunksize=1)
+        lups = sum(r[0] for r in res)
+        wall = max(r[2] for r in res) - min(r[1] for r in res)
+        return lups / wall / 1e9, wall, lups
+
+    def cg_iteration_s(self, iters=2):
+        """Seconds per oracle coarse-CG iteration (one core)."""
+        return self.pool.apply(_oracle_cg_task, (iters,)) / iters
+
+    def close(self):
+        self.pool.terminate()
+        self.pool.join()
+
+
+def host_cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return None
+
+
+def oracle_sample_steps(p):
+    """Fine steps per slice of one bounded oracle sample (about a second or two of
+    numpy per core at the workload's full grid)."""
+    M = 1
+    for v in p["n"]:
+        M *= v
+    if p.get("f_scheme") == "cn":
+        return 2
+    return max(1, min(p["f_steps"], int(2.5e7 // M)))
+
+
+def oracle_time_to_tol_s(p, fine_s_per_step_slice, cg_it_s, cores, k, cg_iterations):
+    """Time of the oracle's synchronous Parareal solve on `cores` host cores,
+    extrapolated (labelled as such): the fine phase of iteration j runs the
+    N - j active slices' F spread over the cores, the coarse sweep and the
+    predictor are sequential CG solves.  Work counts (k, CG iterations) are the
+    GPU run's; per-unit costs are the oracle's, measured on this host."""
+    N, nf = p["N"], p["f_steps"]
+    fine = sum(math.ceil((N - j) / cores) for j in range(k)) * nf * fine_s_per_step_slice
+    return fine + cg_iterations * cg_it_s
+
+
+def cpu_baseline_leg(name, p, over, gpu_stats=None):
+    """cpu_baseline object of the bench line: the oracle's fine GLUP/s on all
+    host cores (bounded sample), plus the extrapolated oracle time-to-tolerance
+    when the GPU run's work counts are given."""
+    t_start = time.perf_counter()
+    steps = oracle_sample_steps(p)
+    pool = OraclePool(name, over)
+    try:
+        pool.fine(1)                              # warm-up: spawn, imports, inputs
+        v, wall, lups = pool.fine(steps)
+        out = {"value": v, "unit": "GLUP/s", "cores": pool.cores, "kind": "oracle",
+               "cpu": host_cpu_model(),
+               "sample": "oracle F (numpy FP64, one single-threaded process per core) on %d "
+                         "slices x %d fine steps of the full %s grid at once, %.1f s" % (
+                             pool.cores, steps, "x".join(map(str, p["n"])), wall)}
+        if gpu_stats is not None and p.get("g_solver") != "thomas":
+            cg_it = pool.cg_iteration_s(2)
+            per_step_slice = wall / steps     # every core ran one slice of `steps` steps
+            k, cgi = gpu_stats["iterations"], gpu_stats["cg_iterations"]
+            t = oracle_time_to_tol_s(p, per_step_slice, cg_it, pool.cores, k, cgi)
+            out["time_to_tol_s_extrapolated"] = t
+            out["time_to_tol_basis"] = (
+                "extrapolated: %d iterations, %d coarse CG iterations (the GPU run's counts); "
+                "oracle F %.3f s per fine step and slice (cores in parallel), oracle CG "
+                "%.3f s per iteration (one core; the sweep is sequential)" % (
+                    k, cgi, per_step_slice, cg_it))
+    finally:
+        pool.close()
+    out["leg_s"] = time.perf_counter() - t_start
+    return out
 
 
 def run_reference(args, world, rank):
+    """The reference arm: the FP64 oracle as it stands, on all host cores, on a
+    bounded sample of the same workload per step (every core propagates one
+    slice by a few fine steps of the full grid)."""
     if rank != 0:
         return 0
     p = problem_of(args.workload)
-    steps_per_sample = 8 if p.get("f_scheme") == "cn" else (64 if p["dim"] == 2 else 4)
-    for _ in range(args.warmup):
-        cpu_sample(p, 1, steps_per_sample)
-    tot_t, tot_l = 0.0, 0
-    for _ in range(args.steps):
-        _, dt, l = cpu_sample(p, 1, steps_per_sample)
-        tot_t += dt
-        tot_l += l
+    base, over = preset_args(args.workload)
+    steps = oracle_sample_steps(p)
+    pool = OraclePool(base, over)
+    try:
+        pool.fine(1)
+        for _ in range(args.warmup):
+            pool.fine(steps)
+        tot_t, tot_l = 0.0, 0
+        for _ in range(args.steps):
+            _, wall, lups = pool.fine(steps)
+            tot_t += wall
+            tot_l += lups
+        cores = pool.cores
+    finally:
+        pool.close()
     v = tot_l / tot_t / 1e9
-    sample = (f"oracle F (numpy FP64) on 1 slice x {steps_per_sample} fine steps of the "
-              f"full {'x'.join(map(str, p['n']))} grid per step")
+    sample = ("oracle F (numpy FP64, one single-threaded process per core) on %d slices x %d "
+              "fine steps of the full %s grid at once per step" % (
+                  cores, steps, "x".join(map(str, p["n"]))))
     out = {"impl": "reference", "metric": "fine GLUP/s", "value": v, "unit": "GLUP/s",
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": tot_t / args.steps * 1e3, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOADS[args.workload]},
-           "cpu_baseline": {"value": v, "unit": "GLUP/s", "cores": 1, "kind": "oracle",
-                            "sample": sample},
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic", "config": bench_config(args, p, world),
+           "cpu_baseline": {"value": v, "unit": "GLUP/s", "cores": cores, "kind": "oracle",
+                            "cpu": host_cpu_model(), "sample": sample},
            "e2e": {"value": v, "unit": "GLUP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
     return 0
 
 
+def apply_coarse_options(pr, ctx, args):
+    if args.g_cheb:
+        pr.parareal_set_option(ctx, pr.PR_OPT_G_CHEBYSHEV, args.g_cheb)
+    if args.g_cg:
+        pr.parareal_set_option(ctx, pr.PR_OPT_G_CG, args.g_cg)
+
+
 def mixed_vs_fp64(pr, torch, p, u0, lam_mixed, t_mixed_ms, args, local):
-    """The same solve with FP64 fine steps, and the accuracy of both against the
-    FP64 serial fine solution: err = max_i ||lam_i - lam*_i||_inf / max_i ||lam*_i||_inf."""
-    N, M = p["N"], u0.numel()
-    ctx = pr.parareal_create(local, torch.cuda.current_stream())
+    """The same solve with FP64 fine steps (same coarse solver and options), and
+    the accuracy of both against the FP64 serial fine solution:
+    err = max_i ||lam_i - lam*_i||_inf / max_i ||lam*_i||_inf.  The FP64 solve
+    is timed on min(steps, 2) solves after one warm-up (it is the slower arm)."""
+    stream = torch.cuda.current_stream()
+    ctx = pr.parareal_create(local, stream)
     try:
         prob = problem_struct(pr, p, u0, None, f_prec=64)
         pr.parareal_set_problem(ctx, prob)
-        if args.g_cheb:
-            pr.parareal_set_option(ctx, pr.PR_OPT_G_CHEBYSHEV, args.g_cheb)
+        apply_coarse_options(pr, ctx, args)
         lam64 = torch.empty_like(lam_mixed)
-        for _ in range(max(1, min(args.warmup, 1))):
-            pr.parareal_run_sync(ctx, lam64)
+        pr.parareal_run_sync(ctx, lam64)
+        n64 = max(1, min(args.steps, 2))
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        k64 = 0
-        ev0.record()
-        for _ in range(args.steps):
-            _, st = pr.parareal_run_sync(ctx, lam64)
-            k64 = st.iterations
-        ev1.record()
         torch.cuda.synchronize()
-        t64 = ev0.elapsed_time(ev1) / args.steps
+        ev0.record(stream)
+        for _ in range(n64):
+            _, st = pr.parareal_run_sync(ctx, lam64)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        t64 = ev0.elapsed_time(ev1) / n64
         star = torch.empty_like(lam_mixed)
         sst = pr.parareal_serial_fine(ctx, star)
         scale = star.abs().max().item()
         err_m = (lam_mixed - star).abs().max().item() / scale
         err_64 = (lam64 - star).abs().max().item() / scale
         return {"t_mixed_ms": t_mixed_ms, "t_fp64_ms": t64, "speedup": t64 / t_mixed_ms,
-                "err_mixed": err_m, "err_fp64": err_64, "k_fp64": k64,
+                "fp64_solves_timed": n64,
+                "err_mixed": err_m, "err_fp64": err_64, "k_fp64": st.iterations,
                 "fp64_t_fine_ms": st.t_fine_ms, "fp64_t_coarse_ms": st.t_coarse_ms,
                 "fp64_cg_iterations": st.cg_iterations, "g_rtol": p["g_rtol"],
                 "serial_fine_fp64_ms": sst.t_total_ms,
@@ -616,6 +779,33 @@ def run_adjoint_async_workload(args, local):
     return 0
 
 
+# FP64 instructions per point of one coarse CG iteration (constant kappa, the
+# operator scaled by 1/R_x): textbook CG d DADD + d DFMA for B p plus 5 DFMA (p.q,
+# x, r, r.r, p); single-reduction d + d for B r plus 6 DFMA (p, s, x, r, r.r, w.r).
+CG_OPS_PER_POINT = {("textbook", 2): 9, ("textbook", 3): 11, ("single", 2): 10, ("single", 3): 12}
+CG_L2_POINTS = 1 << 21   # the library's automatic choice: single-reduction up to here
+
+
+def fp64_peaks(pr, torch, sm_max_mhz):
+    """The FP64-pipe peak two ways: derived from unit counts and clocks (152 SMs
+    x 2 FP64 instructions per clock per SM x the maximum SM clock: the nominal
+    1.25 TFLOP/s FP64 of this part) and measured by the library's DFMA/DADD
+    throughput probe on this device."""
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    sms = props.multi_processor_count
+    mhz = sm_max_mhz or 2070.0
+    derived = sms * 2 * mhz * 1e6 / 1e9
+    out = {"derived_gops": derived, "derived_basis": "%d SMs x 2 FP64 instr/clk x %.0f MHz" % (
+        sms, mhz), "unit": "G FP64 instr/s"}
+    try:
+        dfma, _ = pr.parareal_probe_fp64(0, 1 << 16)
+        dadd, _ = pr.parareal_probe_fp64(1, 1 << 16)
+        out.update({"probe_dfma_gops": dfma / 1e9, "probe_dadd_gops": dadd / 1e9})
+    except Exception as e:   # the probe is a measurement aid; the bench line stands without it
+        out["probe_error"] = str(e)
+    return out
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -642,8 +832,7 @@ def run_ours(args, world, rank, local):
         pr.parareal_set_option(ctx, pr.PR_OPT_PIPELINE, 1)
         pr.parareal_set_option(ctx, pr.PR_OPT_PIPELINE_CHUNKS, args.chunks)
         pr.parareal_set_option(ctx, pr.PR_OPT_CG_BLOCKS_PER_SM, args.cg_bps)
-    if args.g_cheb:
-        pr.parareal_set_option(ctx, pr.PR_OPT_G_CHEBYSHEV, args.g_cheb)
+    apply_coarse_options(pr, ctx, args)
     lam = torch.empty((N + 1) * M, dtype=torch.float64, device="cuda")
     if args.profile:
         code, st = pr.parareal_run_sync(ctx, lam)
@@ -677,10 +866,11 @@ def run_ours(args, world, rank, local):
     value /= 1e9
     ms = sec * 1e3
     launches = sum(s["launches"] for s in stats)
-    # Roofline of the dominant kernel (the fine step): its launches are timed by
-    # events on the library's stream around every batched F.  Under the pipelined
-    # schedule the fine chunks overlap the coarse sweep, so the kernel is timed on
-    # one extra solve with the plain schedule (same work, same kernels).
+    clk_sum = clk.summary()
+    # Roofline of the fine step: its launches are timed by events on the
+    # library's stream around every batched F.  Under the pipelined schedule the
+    # fine chunks overlap the coarse sweep, so the kernel is timed on one extra
+    # solve with the plain schedule (same work, same kernels).
     roof_stats = stats
     if args.pipeline:
         pr.parareal_set_option(ctx, pr.PR_OPT_PIPELINE, 0)
@@ -689,6 +879,8 @@ def run_ours(args, world, rank, local):
         pr.parareal_set_option(ctx, pr.PR_OPT_PIPELINE, 1)
     lups_r = sum(s["fine_lups"] for s in roof_stats)
     t_fine = sum(s["t_fine_ms"] for s in roof_stats)
+    t_coarse = sum(s["t_coarse_ms"] for s in roof_stats)
+    cg_its = sum(s["cg_iterations"] for s in roof_stats)
     # the explicit F is one launch per fine step; the 1D implicit F and the
     # trapezoidal F (one cooperative launch over the batch) one launch per batch
     fine_launches = sum(s["iterations"] for s in roof_stats) * (
@@ -698,56 +890,84 @@ def run_ours(args, world, rank, local):
     alg_bytes = 2 * b_elem * lups_r  # one read + one write of the state per step
     hbm_peak, peak_kind = peaks()
     fine_glups = lups_r / (t_fine / 1e3) / 1e9
+    fpk = fp64_peaks(pr, torch, clk_sum.get("sm_max_mhz"))
+    fp64_peak = fpk["derived_gops"]
+    fp64_meas = fpk.get("probe_dfma_gops")
+
+    def alu_roof(ops, t_ms, kernel, extra=None):
+        r = {"bound": "alu", "achieved": ops / (t_ms / 1e3) / 1e9, "peak": fp64_peak,
+             "unit": "G FP64 instr/s", "traffic": None, "kernel": kernel,
+             "peak_kind": "derived from unit counts and clocks (" + fpk["derived_basis"] + ")"}
+        r["frac"] = r["achieved"] / r["peak"]
+        if fp64_meas:
+            r["peak_measured"] = fp64_meas
+            r["frac_of_measured"] = r["achieved"] / fp64_meas
+        if extra:
+            r.update(extra)
+        return r
+
     if is_mixed:
         roof = {"bound": "hbm", "achieved": alg_bytes / (t_fine / 1e3) / 1e9, "peak": hbm_peak,
                 "unit": "GB/s", "traffic": None,
                 "kernel": ("step3d_tma (TMA-fed FP32 steps; first/last step step3d_v4)"
                            if p["n"][0] % 4 == 0 and p.get("kappa") is None else "step3d_v4<float>"),
                 "peak_kind": peak_kind}
+        roof["frac"] = roof["achieved"] / roof["peak"]
     elif is_cn:
         f_its = sum(s["fine_cg_iterations"] for s in roof_stats)
         ops = CN_OPS_PER_CG_POINT[dim] * f_its * M + CN_OPS_PER_LUP[dim] * lups_r
-        roof = {"bound": "alu", "achieved": ops / (t_fine / 1e3) / 1e9, "peak": NOMINAL_FP64_OPS,
-                "unit": "Gop/s", "traffic": None, "kernel": "cn_kernel (team CG per trapezoidal step)",
-                "peak_kind": "nominal FP64 (1.25 TFLOP/s = 625 G DFMA/s)",
-                "fine_cg_iterations_per_step": f_its / max(lups_r / M, 1)}
+        roof = alu_roof(ops, t_fine, "cn_kernel (team CG per trapezoidal step)",
+                        {"fine_cg_iterations_per_step": f_its / max(lups_r / M, 1)})
     else:
         ops = fp64_ops_per_lup(p) * lups_r
-        roof = {"bound": "alu", "achieved": ops / (t_fine / 1e3) / 1e9, "peak": NOMINAL_FP64_OPS,
-                "unit": "Gop/s", "traffic": None,
-                "kernel": ("tri_solve (partition Thomas/PCR)" if dim == 1
-                           else f"step{2 if dim == 2 else 3}d<double>"),
-                "peak_kind": "nominal FP64 (1.25 TFLOP/s = 625 G DFMA/s)",
-                "hbm_view": {"achieved_gbs": alg_bytes / (t_fine / 1e3) / 1e9, "peak_gbs": hbm_peak,
-                             "frac": alg_bytes / (t_fine / 1e3) / 1e9 / hbm_peak}}
-    roof["frac"] = roof["achieved"] / roof["peak"]
+        # algorithmic flops of one explicit update u - dt A u: 2d + 2 (6 for the
+        # 5-point stencil, 8 for the 7-point one); an FMA counts 2 against the peak
+        fpl = 2 * dim + 2 if p.get("f_scheme", "explicit") == "explicit" else None
+        flop_view = None
+        if fpl:
+            af = fpl * lups_r / (t_fine / 1e3) / 1e9
+            flop_view = {"flops_per_lup": fpl, "achieved_gflops": af,
+                         "peak_gflops": 2 * fp64_peak, "frac": af / (2 * fp64_peak)}
+        roof = alu_roof(ops, t_fine, ("tri_solve (partition Thomas/PCR)" if dim == 1
+                                      else f"step{2 if dim == 2 else 3}d<double>"),
+                        {"fp64_instr_per_lup": fp64_ops_per_lup(p), "flop_view": flop_view,
+                         "hbm_view": {"achieved_gbs": alg_bytes / (t_fine / 1e3) / 1e9,
+                                      "peak_gbs": hbm_peak,
+                                      "frac": alg_bytes / (t_fine / 1e3) / 1e9 / hbm_peak}})
     roof["avg_launch_ms"] = t_fine / max(fine_launches, 1)
     lups_per_launch = lups_r / max(fine_launches, 1)
     roof["algorithmic_bytes_per_launch"] = 2 * b_elem * lups_per_launch
     tpl = NCU_TRAFFIC_PER_LUP.get(args.workload)
     roof["traffic"] = tpl * lups_per_launch if tpl else None
+    # coarse sweep (the predictor and the corrections' CG solves): FP64 pipe
+    roof_coarse = None
+    if p.get("g_solver") != "thomas" and not args.g_cheb and p.get("kappa") is None:
+        rec = ("single" if args.g_cg == 2 or (args.g_cg == 0 and M <= CG_L2_POINTS)
+               else "textbook")
+        ops_g = CG_OPS_PER_POINT[(rec, dim)] * cg_its * M
+        roof_coarse = alu_roof(ops_g, t_coarse, "cg_kernel (%s CG recurrence)" % rec,
+                               {"cg_iterations": cg_its,
+                                "us_per_cg_iteration": t_coarse * 1e3 / max(cg_its, 1),
+                                "note": "coarse-phase time includes each solve's start and "
+                                        "fused-correction passes"})
+    elif p.get("g_solver") != "thomas":
+        roof_coarse = {"kernel": "cg_kernel (Chebyshev-preconditioned CG, %d FP32 steps)" % args.g_cheb
+                       if args.g_cheb else "cg_kernel",
+                       "cg_iterations": cg_its,
+                       "us_per_cg_iteration": t_coarse * 1e3 / max(cg_its, 1)}
     out = {"metric": "fine GLUP/s", "value": value, "unit": "GLUP/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32/f64" if is_mixed else "f64", "data": "synthetic",
-           "config": {"workload": WORKLOADS[args.workload], "grid": list(p["n"]), "N": N,
-                      "f_steps": p["f_steps"], "tol": p["tol"],
-                      "parallelism": "replicas" if world > 1 else "1 GPU",
-                      "schedule": ("pipelined (F of k+1 overlaps the sweep of k)"
-                                   if args.pipeline else "plain"),
-                      "coarse_solver": ("Thomas (partition tridiagonal solver)"
-                                        if p.get("g_solver") == "thomas" else
-                                        "CG preconditioned by %d FP32 Chebyshev steps" % args.g_cheb
-                                        if args.g_cheb else "CG"),
-                      "l2": "inputs larger than L2 (trajectory %.2f GB + workspaces)" % (
-                          (N + 1) * M * 8 / 1e9)},
+           "config": bench_config(args, p, world),
            "iterations": stats[-1]["iterations"], "time_to_tol_ms": ms / args.steps,
            "fine_phase_glups": fine_glups,
            "t_fine_ms_per_solve": t_fine / len(roof_stats),
-           "t_coarse_ms_per_solve": sum(s["t_coarse_ms"] for s in roof_stats) / len(roof_stats),
+           "t_coarse_ms_per_solve": t_coarse / len(roof_stats),
            "cg_iterations_per_step": sum(s["cg_iterations"] for s in stats) / args.steps,
            "cost_model": cost_model_sync(p, roof_stats[-1], roof_stats[-1]["t_total_ms"]),
-           "roofline": roof, "gpu_launches": launches}
+           "roofline": roof, "roofline_coarse": roof_coarse, "fp64_peak": fpk,
+           "gpu_launches": launches}
     # GPU serial fine solve on the same problem (time-to-solution reference)
     sf = torch.empty_like(lam)
     sst = pr.parareal_serial_fine(ctx, sf)
@@ -758,9 +978,14 @@ def run_ours(args, world, rank, local):
     out["max_abs_vs_serial_fine"] = diff
     del sf
     if is_mixed:
-        out["mixed_vs_fp64"] = mixed_vs_fp64(pr, torch, p, u0, lam, ms / args.steps, args, local)
-    # end-to-end through the host-buffer entry point (pinned host memory)
+        mv = mixed_vs_fp64(pr, torch, p, u0, lam, ms / args.steps, args, local)
+        mv["serial_fine_fp32_ms"] = sst.t_total_ms
+        out["mixed_vs_fp64"] = mv
+        out["speedup_vs_gpu_serial_fine_fp64"] = mv["serial_fine_fp64_ms"] / (ms / args.steps)
+    # end-to-end through the host-buffer entry point (pinned host memory); long
+    # solves are timed on at most three of them
     if not args.no_e2e:
+        e_steps = args.steps if ms / args.steps < 3000 else max(1, min(args.steps, 3))
         u0h = torch.from_numpy(p["u0"].reshape(-1).copy()).pin_memory()
         outh = torch.empty((N + 1) * M, dtype=torch.float64).pin_memory()
         pr.parareal_run_sync_host(ctx, u0h, outh)
@@ -768,7 +993,7 @@ def run_ours(args, world, rank, local):
         with Clocks(local) as clk_e:
             t0 = time.perf_counter()
             e_lups = 0
-            for _ in range(args.steps):
+            for _ in range(e_steps):
                 _, st = pr.parareal_run_sync_host(ctx, u0h, outh)
                 e_lups += st.fine_lups
             torch.cuda.synchronize()
@@ -776,21 +1001,15 @@ def run_ours(args, world, rank, local):
         e_value, _ = replica_aggregate(e_lups, e_sec, world, "cuda")
         out["e2e"] = {"value": e_value / 1e9, "unit": "GLUP/s",
                       "h2d_bytes_per_step": M * 8, "d2h_bytes_per_step": (N + 1) * M * 8,
-                      "ms_per_step": e_sec * 1e3 / args.steps, "clocks": clk_e.summary()}
-    out["clocks"] = clk.summary()
+                      "steps": e_steps, "ms_per_step": e_sec * 1e3 / e_steps,
+                      "clocks": clk_e.summary()}
+        del outh
+    out["clocks"] = clk_sum
+    stats_last = dict(roof_stats[-1])
     pr.parareal_destroy(ctx)
     if rank == 0 and not args.no_cpu:
-        if p.get("f_scheme") == "cn":
-            slices, steps = 1, 10
-        elif dim == 2:
-            slices, steps = 2, p["f_steps"]
-        else:
-            slices, steps = 1, 4
-        v, dt, l = cpu_sample(p, slices=slices, steps=steps)
-        out["cpu_baseline"] = {"value": v, "unit": "GLUP/s", "cores": 1, "kind": "oracle",
-                               "sample": "oracle F (numpy FP64, single thread) on %d slice(s) x "
-                                         "%d fine steps of the full grid, %.1f s" % (
-                                             slices, steps, dt)}
+        base, over = preset_args(args.workload)
+        out["cpu_baseline"] = cpu_baseline_leg(base, p, over, stats_last)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -807,6 +1026,9 @@ def main():
         SIZE_OVERRIDE["n"] = tuple(int(v) for v in args.grid.split(","))
     if args.slices:
         SIZE_OVERRIDE["N"] = args.slices
+    if args.g_cheb is None:
+        from synthetic.configs import PRESETS
+        args.g_cheb = int(PRESETS[preset_args(args.workload)[0]].get("g_cheb", 0))
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         return run_reference(args, world, rank)

@@ -35,6 +35,7 @@ constexpr int CHEB_MAX = 64;
 
 struct ChebDev {
   int m;                      // 0: plain CG
+  int vec;                    // 1: vectorised three-term steps (dim >= 2, kappa = 1, nx % 4 == 0)
   double lo, hi;              // spectrum bounds of B
   float inv_c;                // 1 / centre of [lo, hi]
   float c1[CHEB_MAX], c2[CHEB_MAX];  // step k: d_k = c1[k] d_{k-1} + c2[k] res_k
@@ -158,6 +159,140 @@ __device__ __forceinline__ double cheb_step(const Geom& g, const ChebDev& ch, bo
   return acc;
 }
 
+// Vectorised Chebyshev step in three-term form (constant kappa, dim >= 2,
+// nx % 4 == 0).  The d-form above, d_k = c1 d_{k-1} + c2 (f - B y_k),
+// y_{k+1} = y_k + d_k with d_{k-1} = y_k - y_{k-1}, is the same recurrence as
+//     y_{k+1} = y_k + c1 (y_k - y_{k-1}) + c2 (f - B y_k),      y_0 = 0,
+// which reads y_k (with its stencil), y_{k-1} and f and writes y_{k+1}: 16
+// bytes per point instead of 24.  A warp owns 128 consecutive x (one float4
+// per lane) of one row of the middle axis (y in 3D) and streams CV_ZC planes
+// of the slowest axis (z in 3D, y in 2D), carrying the previous, current and
+// next plane of y_k in registers; x-neighbours come from the adjacent lanes by
+// shuffles (the warp's two edge values by one scalar load each), middle-axis
+// neighbours by float4 loads.  The last step writes z = y_m in FP64 and
+// returns this thread's part of r.z.
+constexpr int CV_ZC = 8;
+
+__device__ __forceinline__ float4 ldf4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+
+template <int DIM, bool FIRST, bool LAST>
+__device__ __forceinline__ double cheb3_step(const Geom& g, const ChebDev& ch,
+                                             const float* __restrict__ yk,
+                                             const float* __restrict__ ykm,
+                                             const float* __restrict__ f, float* __restrict__ yn,
+                                             double* __restrict__ z, const double* __restrict__ r,
+                                             float c1, float c2, int blk, int nblk) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  const long long gw = (long long)blk * wpb + (threadIdx.x >> 5);
+  const long long nw = (long long)nblk * wpb;
+  const int nx = g.nx;
+  const int ns = DIM == 3 ? g.nz : g.ny;             // streamed axis
+  const int nm = DIM == 3 ? g.ny : 1;                // middle axis
+  const long long sst = DIM == 3 ? (long long)g.nx * g.ny : (long long)g.nx;
+  const int XC = (nx + 127) >> 7;
+  const int SC = (ns + CV_ZC - 1) / CV_ZC;
+  const long long items = (long long)XC * nm * SC;
+  const float c0 = ch.c0, rx = ch.rx;
+  const float rm = DIM == 3 ? ch.ry : 0.f;           // middle-axis coupling
+  const float rs = DIM == 3 ? ch.rz : ch.ry;         // streamed-axis coupling
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  double acc = 0.0;
+  for (long long j = gw; j < items; j += nw) {
+    const int xc = (int)(j % XC);
+    const long long t = j / XC;
+    const int ym = (int)(t % nm);
+    const int s0 = (int)(t / nm) * CV_ZC;
+    const int s1 = min(s0 + CV_ZC, ns);
+    const int x = xc * 128 + 4 * lane;
+    const bool act = x < nx;
+    const long long row = (DIM == 3 ? (long long)ym * nx : 0) + x;
+    float4 prv = zero, cur = zero;
+    if (act) {
+      if (s0 > 0) prv = ldf4(yk + (s0 - 1) * sst + row);
+      cur = ldf4(yk + s0 * sst + row);
+    }
+    for (int sl = s0; sl < s1; ++sl) {
+      const long long o = sl * sst + row;
+      float4 nxt = zero, mid = zero, fv = zero, pv = zero;
+      float wv = 0.f, ev = 0.f;
+      if (act) {
+        if (sl + 1 < ns) nxt = ldf4(yk + o + sst);
+        if (DIM == 3) {
+          if (ym > 0) mid = ldf4(yk + o - nx);
+          if (ym + 1 < nm) {
+            const float4 q = ldf4(yk + o + nx);
+            mid.x += q.x;
+            mid.y += q.y;
+            mid.z += q.z;
+            mid.w += q.w;
+          }
+        }
+        fv = ldf4(f + o);
+        if (!FIRST) pv = ldf4(ykm + o);
+        if (lane == 0 && x > 0) wv = yk[o - 1];
+        if (lane == 31 && x + 4 < nx) ev = yk[o + 4];
+      }
+      const float wsh = __shfl_up_sync(FULL, cur.w, 1);
+      const float esh = __shfl_down_sync(FULL, cur.x, 1);
+      if (lane > 0) wv = wsh;
+      if (lane < 31) ev = esh;
+      // B y at the four points, then y_{k+1}
+      float4 out;
+      {
+        const float b0 = c0 * cur.x - rx * (wv + cur.y) - rm * mid.x - rs * (prv.x + nxt.x);
+        const float b1 = c0 * cur.y - rx * (cur.x + cur.z) - rm * mid.y - rs * (prv.y + nxt.y);
+        const float b2 = c0 * cur.z - rx * (cur.y + cur.w) - rm * mid.z - rs * (prv.z + nxt.z);
+        const float b3 = c0 * cur.w - rx * (cur.z + ev) - rm * mid.w - rs * (prv.w + nxt.w);
+        out.x = cur.x + c1 * (cur.x - pv.x) + c2 * (fv.x - b0);
+        out.y = cur.y + c1 * (cur.y - pv.y) + c2 * (fv.y - b1);
+        out.z = cur.z + c1 * (cur.z - pv.z) + c2 * (fv.z - b2);
+        out.w = cur.w + c1 * (cur.w - pv.w) + c2 * (fv.w - b3);
+      }
+      if (act) {
+        if (LAST) {
+          const double2 z01 = make_double2(out.x, out.y), z23 = make_double2(out.z, out.w);
+          double2* zp = reinterpret_cast<double2*>(z + o);
+          zp[0] = z01;
+          zp[1] = z23;
+          const double2* rp = reinterpret_cast<const double2*>(r + o);
+          const double2 r01 = rp[0], r23 = rp[1];
+          acc = fma(r01.x, z01.x, acc);
+          acc = fma(r01.y, z01.y, acc);
+          acc = fma(r23.x, z23.x, acc);
+          acc = fma(r23.y, z23.y, acc);
+        } else {
+          *reinterpret_cast<float4*>(yn + o) = out;
+        }
+      }
+      prv = cur;
+      cur = nxt;
+    }
+  }
+  return acc;
+}
+
+// Steps k = 1..m-1 of the vectorised preconditioner: y_1 = f / c is in ring
+// slot 1 (written with f by the pass that updated r), y_k in slot k % 3.
+template <int DIM>
+__device__ __forceinline__ double cheb3_dispatch(const Geom& g, const ChebDev& ch,
+                                                 const double* __restrict__ r, int kk, int blk,
+                                                 int nblk) {
+  const int sk = kk % 3;
+  const float c1 = ch.c1[kk], c2 = ch.c2[kk];
+  const float* yk = sk == 0 ? ch.y : sk == 1 ? ch.d0 : ch.d1;
+  const float* ykm = sk == 0 ? ch.d1 : sk == 1 ? ch.y : ch.d0;
+  float* yn = sk == 0 ? ch.d0 : sk == 1 ? ch.d1 : ch.y;
+  const bool last = kk == ch.m - 1;
+  if (kk == 1) {
+    if (last) return cheb3_step<DIM, true, true>(g, ch, yk, ykm, ch.res, yn, ch.z, r, c1, c2, blk, nblk);
+    return cheb3_step<DIM, true, false>(g, ch, yk, ykm, ch.res, yn, ch.z, r, c1, c2, blk, nblk);
+  }
+  if (last) return cheb3_step<DIM, false, true>(g, ch, yk, ykm, ch.res, yn, ch.z, r, c1, c2, blk, nblk);
+  return cheb3_step<DIM, false, false>(g, ch, yk, ykm, ch.res, yn, ch.z, r, c1, c2, blk, nblk);
+}
+
 // Preconditioned CG (Hestenes-Stiefel with z = p_m(B) r), same start, stopping
 // rule and return value as cg_core.  Per iteration: q = B p and p.q (reduction);
 // x, r and r.r, which also starts the preconditioner res = r, d_0 = res / c,
@@ -223,7 +358,10 @@ __device__ int pcg_core(const CgDev& a, int nblk, int blk) {
       float* dn = (kk & 1) ? ch.d1 : ch.d0;
       const bool last = kk == ch.m - 1;
       double s_rz = 0.0;
-      if (last)
+      if (ch.vec)
+        s_rz = g.dim == 3 ? cheb3_dispatch<3>(g, ch, ws.r, kk, blk, nblk)
+                          : cheb3_dispatch<2>(g, ch, ws.r, kk, blk, nblk);
+      else if (last)
         s_rz = cheb_step<true>(g, ch, var, dp, dn, ch.res, ch.y, ch.z, ws.r, c1, c2, blk, nblk);
       else
         cheb_step<false>(g, ch, var, dp, dn, ch.res, ch.y, ch.z, ws.r, c1, c2, blk, nblk);
@@ -401,6 +539,7 @@ cudaError_t cg_solve(pr_ctx* c, const CgArgs& in) {
   if (c->opt_g_cheb >= 2 && c->cheb_z) {
     ChebDev& ch = a.ch;
     ch.m = c->opt_g_cheb;
+    ch.vec = (c->g.dim >= 2 && !c->var_kappa && c->g.nx % 4 == 0) ? 1 : 0;
     ch.lo = c->g_lo;
     ch.hi = c->g_hi;
     // Chebyshev recurrence coefficients on [lo, hi] (centre cc, half width ee)

@@ -50,7 +50,8 @@ def test_reference_arm_prints_one_contract_line():
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference",
-                          "--steps", "1", "--warmup", "3"], capture_output=True, text=True,
+                          "--steps", "1", "--warmup", "3", "--grid", "96,80", "--slices", "4",
+                          "--workload", "heat2d_explicit"], capture_output=True, text=True,
                          check=True, timeout=600, cwd=root).stdout.strip().splitlines()
     lines = [ln for ln in out if ln.startswith("{")]
     assert len(lines) == 1
@@ -61,6 +62,10 @@ def test_reference_arm_prints_one_contract_line():
         assert key in d, key
     assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 1
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] == os.cpu_count()          # every host core
+    for key in ("grid", "N", "f_steps", "tol", "g_rtol"):           # the GPU line's config keys
+        assert key in d["config"], key
+    assert d["config"]["grid"] == [96, 80] and d["config"]["N"] == 4
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert "workload" in d["config"]
 
@@ -78,3 +83,12 @@ def test_proposition3_reproduces_the_papers_table1_estimates():
         est = bench.apr_cost(int(p), int(kappa), 100 * C_G, C_G)
         tol = 0.015 if p == "16" else 0.001
         assert abs(est - float(printed)) <= tol * float(printed), (p, est, printed)
+
+
+def test_oracle_time_to_tol_extrapolation_counts_the_work():
+    """The extrapolated oracle time: the fine phase of iteration j spreads the
+    N - j active slices over the cores; the coarse CG iterations run in sequence."""
+    p = {"N": 10, "f_steps": 4}
+    # k = 2: ceil(10/4) + ceil(9/4) = 3 + 3 rounds of 4 steps at 0.5 s, plus 7 CG x 2 s
+    t = bench.oracle_time_to_tol_s(p, 0.5, 2.0, 4, 2, 7)
+    assert abs(t - (6 * 4 * 0.5 + 14.0)) < 1e-12

@@ -18,7 +18,8 @@ pytestmark = pytest.mark.gpu
 
 
 def case(name, **over):
-    p = preset(name, "small")
+    sizes = {k: over.pop(k) for k in ("n", "N", "f_steps") if k in over}
+    p = preset(name, "small", **sizes)
     p.update(dict(g_rtol=1e-13, f_prec=64))
     p.update(over)
     return p
@@ -47,6 +48,46 @@ def test_pcg_coarse_solve(name, m):
     assert np.linalg.norm(r) <= 1e-12 * np.linalg.norm(b)
     if m == 8:
         assert it < plain_it
+
+
+@pytest.mark.parametrize("n", [(132, 61), (4, 9), (256, 37), (136, 30, 19), (8, 5, 3),
+                               (128, 16, 17)])
+@pytest.mark.parametrize("m", [2, 3, 12])
+def test_pcg_vectorised_steps(n, m):
+    """Constant kappa with nx % 4 == 0 takes the vectorised three-term Chebyshev
+    steps (128 x per warp, streamed slowest axis): ragged x chunks (a chunk with
+    one or two active lanes), ragged plane runs, single-lane rows, m = 2 (the first
+    step is also the last) and m = 3 (first and last distinct)."""
+    name = "heat2d_explicit" if len(n) == 2 else "heat3d_mixed"
+    p = case(name, g_cheb=m, n=n)
+    rng = np.random.default_rng(64)
+    shape = tuple(reversed(n))
+    b = rng.standard_normal(shape)
+    x0 = b + 0.1 * rng.standard_normal(shape)
+    P = heat.Propagators(p)
+    ref, ref_it = P.G(b, x0=x0)
+    with Ctx(p) as c:
+        pr.parareal_set_option(c.ctx, pr.PR_OPT_G_CHEBYSHEV, m)
+        out = torch().empty(c.M, dtype=torch().float64, device="cuda")
+        it = pr.parareal_coarse(c.ctx, dev(b), dev(x0), out)
+        got = host(out).reshape(shape)
+    assert abs(it - ref_it) <= 2, (it, ref_it)
+    assert rel_l2(got, ref) < 1e-12
+    r = b - (got + P.dT * heat.apply_A(got, P.h, P.kappa))
+    assert np.linalg.norm(r) <= 1e-12 * np.linalg.norm(b)
+
+
+def test_pcg_vectorised_sync_parareal_parity():
+    n = (132, 61)
+    p = case("heat2d_explicit", tol=1e-9, g_cheb=8, n=n)
+    ref = sync_parareal(p)
+    with Ctx(p) as c:
+        pr.parareal_set_option(c.ctx, pr.PR_OPT_G_CHEBYSHEV, 8)
+        lam = c.lam()
+        code, st = pr.parareal_run_sync(c.ctx, lam)
+        got = host(lam).reshape(ref.lam.shape)
+    assert code == pr.PR_OK and st.iterations == ref.k
+    assert rel_l2(got, ref.lam) < 1e-11
 
 
 def test_pcg_sync_parareal_parity():
