@@ -7,7 +7,11 @@ residual) and properties that hold at any size:
   * at convergence lambda_i - F(lambda_{i-1}) is of the order of the last
     increments (Eq. (11) with lambda^k ~ lambda^{k-1});
   * the coarse solve meets its residual bound, measured with the oracle's
-    operator.
+    operator;
+  * one correction of Eq. (11) / Algorithm 1 element by element: from the
+    GPU's own iterates lambda^k and lambda^{k+1} the oracle forms
+    (G(lambda_{i-1}^{k+1}) + F(lambda_{i-1}^k)) - G(lambda_{i-1}^k) for sampled
+    slices i and compares it with the GPU's lambda_i^{k+1} at every point.
 """
 import numpy as np
 import pytest
@@ -63,6 +67,59 @@ def test_heat3d_mixed_workload_sampled_parity():
     scale = np.max(np.abs(ref1))
     gap = np.max(np.abs(lN - P64.F(lNm1))) / scale
     assert gap < 1e-5, gap
+
+
+def _iterates(p, k, slices, **over):
+    """Slices `slices` of the GPU's lambda^k (max_iter = k, tol = 0) as host arrays."""
+    shape = tuple(reversed(p["n"]))
+    with Ctx(p, tol=0.0, max_iter=k, **over) as c:
+        if p.get("g_cheb"):
+            pr.parareal_set_option(c.ctx, pr.PR_OPT_G_CHEBYSHEV, p["g_cheb"])
+        lam = c.lam()
+        code, st = pr.parareal_run_sync(c.ctx, lam)
+        assert st.iterations == k
+        out = {i: host(lam[i * c.M:(i + 1) * c.M]).reshape(shape) for i in slices}
+    return out
+
+
+def _correction_parity(p, k, slices, tol, P):
+    """lambda_i^{k+1} against (G(lambda_{i-1}^{k+1}) + F(lambda_{i-1}^k)) - G(lambda_{i-1}^k)
+    computed by the FP64 oracle from the GPU's lambda^k and lambda^{k+1}, for
+    slices i with i - 1 > k (fresh coarse values).  The coarse difference is
+    taken as G(lambda_{i-1}^{k+1} - lambda_{i-1}^k) (G is linear), solved to
+    rtol 1e-14 of that difference.  Slices i <= k are frozen (Algorithm 1)."""
+    need = sorted(set([i - 1 for i in slices] + list(slices) + [1, k]))
+    Lk = _iterates(p, k, need)
+    Lk1 = _iterates(p, k + 1, need)
+    assert np.array_equal(Lk1[k], Lk[k]) and np.array_equal(Lk1[1], Lk[1])   # frozen prefix
+    worst = 0.0
+    for i in slices:
+        assert i - 1 > k
+        d = Lk1[i - 1] - Lk[i - 1]
+        Gd, _ = heat.cg_implicit_euler(d, P.dT, P.h, P.kappa, None, rtol=1e-14, maxit=20000)
+        expect = Gd + P.F(Lk[i - 1])
+        err = np.max(np.abs(Lk1[i] - expect)) / np.max(np.abs(expect))
+        assert rel_l2(Lk1[i], expect) < tol, (i, rel_l2(Lk1[i], expect))
+        assert err < tol, (i, err)
+        worst = max(worst, err)
+    return worst
+
+
+def test_heat2d_bench_workload_correction_parity():
+    """1024^2, N = 64, F = 256 explicit FP64 steps, coarse CG at the parity
+    setting rtol 1e-13: one correction (k = 2 -> 3) at every point of slices 4,
+    32 and 64, within 1e-12."""
+    p = preset("heat2d_explicit", "full")
+    p["g_rtol"] = 1e-13
+    _correction_parity(p, 2, (4, p["N"] // 2, p["N"]), 1e-12, heat.Propagators(p))
+
+
+def test_heat3d_mixed_workload_correction_parity():
+    """256^3, N = 128, FP32 fine / FP64 coarse in the bench's coarse configuration:
+    one correction (k = 2 -> 3) at every point of slice 64 against the FP64
+    oracle, within the mixed-precision tolerance 1e-5."""
+    p = preset("heat3d_mixed", "full")
+    _correction_parity(p, 2, (p["N"] // 2,), 1e-5, heat.Propagators(dict(p, f_prec=64)))
 
 
 def test_heat3d_varkappa_fp32_fine_step_full_size():

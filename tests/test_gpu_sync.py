@@ -443,6 +443,30 @@ def test_pipelined_schedule_is_bitwise_identical(case, chunks, bps):
                 assert rel_l2(host(lam_b), host(lam_a)) < FP64_TOL
 
 
+@pytest.mark.parametrize("case", ["2d_const", "3d_var", "1d_thomas"])
+def test_pipelined_schedule_matches_oracle(case):
+    """The pipelined schedule against Algorithm 1 in the oracle (not only against
+    the plain GPU schedule): the converged run and two capped runs, every point."""
+    p = CASES[case]()
+    p["tol"] = 1e-9 if case != "1d_thomas" else 1e-10
+    ref = sync_parareal(p)
+    rec = sync_parareal(p, tol=0.0, record=True)
+    with Ctx(p) as c:
+        pr.parareal_set_option(c.ctx, pr.PR_OPT_PIPELINE, 1)
+        pr.parareal_set_option(c.ctx, pr.PR_OPT_PIPELINE_CHUNKS, 3)
+        lam = c.lam()
+        code, st = pr.parareal_run_sync(c.ctx, lam)
+        assert st.iterations == ref.k
+        assert rel_l2(host(lam), ref.lam) < FP64_TOL
+        for k in (1, 2):
+            c.prob.max_iter = k
+            c.prob.tol = 0.0
+            pr.parareal_set_problem(c.ctx, c.prob)
+            lam = c.lam()
+            pr.parareal_run_sync(c.ctx, lam)
+            assert rel_l2(host(lam), rec.iterates[k]) < FP64_TOL, k
+
+
 def test_pipelined_schedule_with_iteration_cap_and_bad_options():
     p = CASES["2d_const"]()
     p["tol"] = 1e-14
