@@ -393,15 +393,15 @@ def test_invalid_problems_are_rejected():
 
 
 def test_out_of_memory_problem_leaves_context_usable():
-    """A problem whose trajectory cannot be allocated (65536^2 x 64 slices, about
-    2 TB per array) fails with PR_ENOMEM before anything runs; the context then
-    takes an ordinary problem and solves it as usual."""
+    """A problem whose trajectory cannot be allocated (40000^2 x 64 slices, about
+    0.8 TB per array, within the size limits) fails with PR_ENOMEM before anything
+    runs; the context then takes an ordinary problem and solves it as usual."""
     p = CASES["2d_const"]()
     t = torch()
     ctx = pr.parareal_create(0, t.cuda.current_stream())
     try:
         u0 = dev(p["u0"])
-        huge = pr.make_problem(dim=2, n=(65536, 65536), T0=0.0, T=1e-6, N=64, u0=u0,
+        huge = pr.make_problem(dim=2, n=(40000, 40000), T0=0.0, T=1e-6, N=64, u0=u0,
                                f_steps=16, g_rtol=1e-10, tol=1e-9)
         with pytest.raises(pr.PararealError) as e:
             pr.parareal_set_problem(ctx, huge)
@@ -413,6 +413,29 @@ def test_out_of_memory_problem_leaves_context_usable():
         ref = sync_parareal(p)
         assert code == pr.PR_OK and st.iterations == ref.k
         assert rel_l2(host(lam), ref.lam) < FP64_TOL
+    finally:
+        pr.parareal_destroy(ctx)
+
+
+def test_set_problem_rejects_sizes_beyond_the_limits_without_overflow():
+    """Each axis and the running product are bounded before the next
+    multiplication: three axes of 2^21 (product 2^63, which wraps a signed
+    64-bit integer), a product just above 2^31 - 1, and a trajectory of more
+    than 2^40 points are PR_EINVAL; nothing is allocated or launched."""
+    p = CASES["2d_const"]()
+    t = torch()
+    ctx = pr.parareal_create(0, t.cuda.current_stream())
+    try:
+        u0 = dev(p["u0"])
+        bad = [dict(dim=3, n=(1 << 21, 1 << 21, 1 << 21), N=4),
+               dict(dim=2, n=(65536, 32769), N=4),
+               dict(dim=3, n=(2048, 2048, 256), N=1100),
+               dict(dim=1, n=(16,), N=70000)]
+        for kw in bad:
+            prob = pr.make_problem(T0=0.0, T=1e-6, u0=u0, f_steps=4, g_rtol=1e-10, tol=1e-9, **kw)
+            with pytest.raises(pr.PararealError) as e:
+                pr.parareal_set_problem(ctx, prob)
+            assert e.value.code == pr.PR_EINVAL, kw
     finally:
         pr.parareal_destroy(ctx)
 
