@@ -22,11 +22,14 @@ PRESETS = {
                             small=dict(n=(70, 61), N=8, f_steps=32),
                             tiny=dict(n=(6, 5), N=4, f_steps=4)),
     # coarse CG tolerance 1e-7: the FP32 fine steps' rounding noise floor (the workload
-    # names no CG tolerance; the same setting serves the FP64 comparison arm)
+    # names no CG tolerance; the same setting serves the FP64 comparison arm); the
+    # coarse CG is preconditioned by 12 FP32 Chebyshev steps at full size (the reduced
+    # parity variants run plain CG; the preconditioner has parity cases of its own)
     "heat3d_mixed": dict(dim=3, n=(256, 256, 256), N=128, f_steps=64, f_scheme="explicit",
                          g_solver="cg", dt_h2=0.15, tol=1e-5, g_rtol=1e-7, f_prec=32,
-                         small=dict(n=(37, 30, 26), N=6, f_steps=16),
-                         tiny=dict(n=(4, 3, 3), N=3, f_steps=3)),
+                         g_cheb=12,
+                         small=dict(n=(37, 30, 26), N=6, f_steps=16, g_cheb=0),
+                         tiny=dict(n=(4, 3, 3), N=3, f_steps=3, g_cheb=0)),
     "heat2d_inverse": dict(dim=2, n=(512, 512), N=32, f_steps=128, f_scheme="explicit",
                            g_solver="cg", kappa_seed=40, kappa_star_seed=41, tol=0.0,
                            g_rtol=1e-13, K=6, f_prec=64,

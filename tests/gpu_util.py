@@ -46,6 +46,12 @@ class Ctx:
         self.ctx = pr.parareal_create(0, t.cuda.current_stream())
         self.prob = problem_struct(p, self.u0, self.kappa, **over)
         pr.parareal_set_problem(self.ctx, self.prob)
+        # the coarse solver the oracle runs for this problem (Propagators reads the same keys)
+        if p.get("g_cheb"):
+            pr.parareal_set_option(self.ctx, pr.PR_OPT_G_CHEBYSHEV, p["g_cheb"])
+        if p.get("g_cg"):
+            pr.parareal_set_option(self.ctx, pr.PR_OPT_G_CG,
+                                   {"textbook": 1, "single": 2}[p["g_cg"]])
         self.M = int(np.prod(p["n"]))
         self.N = p["N"]
 

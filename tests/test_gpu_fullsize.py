@@ -72,9 +72,7 @@ def test_heat3d_mixed_workload_sampled_parity():
 def _iterates(p, k, slices, **over):
     """Slices `slices` of the GPU's lambda^k (max_iter = k, tol = 0) as host arrays."""
     shape = tuple(reversed(p["n"]))
-    with Ctx(p, tol=0.0, max_iter=k, **over) as c:
-        if p.get("g_cheb"):
-            pr.parareal_set_option(c.ctx, pr.PR_OPT_G_CHEBYSHEV, p["g_cheb"])
+    with Ctx(p, tol=0.0, max_iter=k, **over) as c:   # Ctx applies the preset's coarse options
         lam = c.lam()
         code, st = pr.parareal_run_sync(c.ctx, lam)
         assert st.iterations == k
