@@ -38,6 +38,11 @@ namespace {
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
+// a coarse solve reports a negative iteration count when a bounded wait of its
+// TMA-fed preconditioner steps expired (its result is then not valid)
+const char* const kCoarseWaitExpired =
+    "coarse solve: a bounded wait of the TMA-fed Chebyshev steps expired";
+
 void free_problem(pr_ctx* c) {
   void* ptrs[] = {c->fcoef, c->fcoef32, c->gcoef, c->fsys0, c->v, c->w, c->tmp, c->f32a, c->f32b,
                   c->tma_err,
@@ -370,6 +375,7 @@ int parareal_coarse(pr_ctx* c, const double* in, const double* x0, double* out, 
     int it = 0;
     PR_CUDA(c, cudaMemcpyAsync(&it, c->cg_iters_dev, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     PR_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (it < 0) return fail(c, PR_ECUDA, kCoarseWaitExpired);
     if (iters) *iters = it;
   }
   PR_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -508,6 +514,7 @@ int parareal_run_sync(pr_ctx* c, double* lam, pr_stats* st) {
   nvtxRangePop();
   cudaEventElapsedTime(&t_g, c->ev[0], c->ev[1]);
   for (int i = 1; i <= N; ++i) {
+    if (iters[i] < 0) return fail(c, PR_ECUDA, kCoarseWaitExpired);
     S.cg_iterations += iters[i];
     S.coarse_solves += 1;
   }
@@ -583,6 +590,7 @@ int parareal_run_sync(pr_ctx* c, double* lam, pr_stats* st) {
       maxd = std::max(maxd, d);
     }
     for (int i = k + 2; i <= N; ++i) {
+      if (iters[i] < 0) return fail(c, PR_ECUDA, kCoarseWaitExpired);
       S.cg_iterations += iters[i];
       S.coarse_solves += 1;
     }

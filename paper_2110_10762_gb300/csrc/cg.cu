@@ -18,6 +18,7 @@
 #include <cooperative_groups.h>
 
 #include "device.cuh"
+#include "tma.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -36,6 +37,8 @@ constexpr int CHEB_MAX = 64;
 struct ChebDev {
   int m;                      // 0: plain CG
   int vec;                    // 1: vectorised three-term steps (dim >= 2, kappa = 1, nx % 4 == 0)
+  const unsigned char* tmaps; // 3D: tensor maps of y, d0, d1 (128 B each, device), or NULL
+  int* err;                   // set to 1 when a bounded wait of the TMA-fed steps expired
   double lo, hi;              // spectrum bounds of B
   float inv_c;                // 1 / centre of [lo, hi]
   float c1[CHEB_MAX], c2[CHEB_MAX];  // step k: d_k = c1[k] d_{k-1} + c2[k] res_k
@@ -273,18 +276,171 @@ __device__ __forceinline__ double cheb3_step(const Geom& g, const ChebDev& ch,
   return acc;
 }
 
+// TMA-fed three-term Chebyshev step (3D, constant kappa, nx % 4 == 0): the same
+// arithmetic as cheb3_step, with y_k staged through shared memory.  The group's
+// blocks take 64 x 16 x CT_ZC bricks round-robin; for each brick one elected
+// thread issues cp.async.bulk.tensor loads of the 72 x 18 planes of y_k (x halo
+// 4 wide so that every load starts on a 16-byte boundary; the copy engine fills
+// zeros outside the grid, the Dirichlet values) into a CT_ST-stage ring, each
+// stage completed on its own mbarrier, two planes ahead of the computed one.
+// f and y_{k-1} (no stencil) come by float4 loads issued before the wait.  A
+// thread computes 4 consecutive x points.  `gl` counts the loads this block has
+// issued in this launch (stage = gl % CT_ST, phase parity = gl / CT_ST); every
+// load is waited before the brick ends.  A wait that expires marks the block
+// dead (it drains its loads, sets ch.err and skips all later TMA work; the
+// solve is reported as failed).
+constexpr int CT_TX = 64, CT_TY = 16, CT_ZC = 16, CT_ST = 4;
+constexpr int CT_PX = CT_TX + 8, CT_PY = CT_TY + 2;
+constexpr unsigned CT_BYTES = CT_PX * CT_PY * sizeof(float);
+constexpr int CT_STRIDE = (int)(((CT_BYTES + 127) / 128) * 128 / sizeof(float));
+constexpr int CT_SMEM = CT_ST * CT_STRIDE * (int)sizeof(float) + CT_ST * 8;
+
+struct ChebTma {
+  float* stage;              // CT_ST stages of CT_STRIDE floats (dynamic shared memory)
+  unsigned long long* bar;   // CT_ST mbarriers
+  unsigned gl;               // loads issued by this block so far (block-uniform)
+  bool dead;                 // a bounded wait expired (block-uniform)
+};
+
+template <bool FIRST, bool LAST>
+__device__ __forceinline__ double cheb_tma_step(const Geom& g, const ChebDev& ch, const void* map,
+                                                const float* __restrict__ ykm,
+                                                const float* __restrict__ f,
+                                                float* __restrict__ yn, double* __restrict__ z,
+                                                const double* __restrict__ r, float c1, float c2,
+                                                int blk, int nblk, ChebTma& tm) {
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int TXn = (g.nx + CT_TX - 1) / CT_TX, TYn = (g.ny + CT_TY - 1) / CT_TY;
+  const int TZn = (g.nz + CT_ZC - 1) / CT_ZC;
+  const long long nbricks = (long long)TXn * TYn * TZn;
+  const long long plane = (long long)g.nx * g.ny;
+  const float c0 = ch.c0, rx = ch.rx, ry = ch.ry, rz = ch.rz;
+  const int c = (ty + 1) * CT_PX + 4 + 4 * tx;  // this thread's first point in a stage
+  double acc = 0.0;
+  for (long long t = blk; t < nbricks && !tm.dead; t += nblk) {
+    const int xt = (int)(t % TXn);
+    const long long u = t / TXn;
+    const int yt = (int)(u % TYn);
+    const int zt = (int)(u / TYn);
+    const int x0 = xt * CT_TX, y0 = yt * CT_TY, z0 = zt * CT_ZC;
+    const int z1 = min(z0 + CT_ZC, g.nz);
+    const int nload = z1 - z0 + 2;   // planes z0-1 .. z1; load index L = plane - (z0 - 1)
+    const unsigned gl = tm.gl;
+    auto issue = [&](int L) {
+      const unsigned q = gl + L;
+      float* dst = tm.stage + (q % CT_ST) * CT_STRIDE;
+      mbar_arrive_expect_tx(&tm.bar[q % CT_ST], CT_BYTES);
+      tma_load_3d(dst, map, x0 - 4, y0 - 1, z0 - 1 + L, &tm.bar[q % CT_ST]);
+    };
+    if (tid == 0) {
+      // the stages were last read through the generic proxy (previous brick or step)
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      for (int L = 0; L < CT_ST && L < nload; ++L) issue(L);
+    }
+    int issued = CT_ST < nload ? CT_ST : nload;
+    int waited = 0;
+    bool ok = true;
+    const int gx = x0 + 4 * tx, gy = y0 + ty;
+    const bool inside = gx < g.nx && gy < g.ny;
+    for (int zi = z0; zi < z1; ++zi) {
+      const int L = zi - z0 + 1;
+      const long long o = zi * plane + (long long)gy * g.nx + gx;
+      float4 fv = make_float4(0.f, 0.f, 0.f, 0.f), pv = fv;
+      if (inside) {
+        fv = ldf4(f + o);
+        if (!FIRST) pv = ldf4(ykm + o);
+      }
+      while (ok && waited <= L + 1) {
+        const unsigned q = gl + waited;
+        ok = mbar_wait(&tm.bar[q % CT_ST], (q / CT_ST) & 1u);
+        if (ok) ++waited;
+      }
+      if (__syncthreads_or(!ok)) {
+        tm.dead = true;
+        break;
+      }
+      if (inside) {
+        const float* Pm = tm.stage + ((gl + L - 1) % CT_ST) * CT_STRIDE;
+        const float* Pc = tm.stage + ((gl + L) % CT_ST) * CT_STRIDE;
+        const float* Pp = tm.stage + ((gl + L + 1) % CT_ST) * CT_STRIDE;
+        const float4 cur = *reinterpret_cast<const float4*>(Pc + c);
+        const float4 s4 = *reinterpret_cast<const float4*>(Pc + c - CT_PX);
+        const float4 n4 = *reinterpret_cast<const float4*>(Pc + c + CT_PX);
+        const float4 b4 = *reinterpret_cast<const float4*>(Pm + c);
+        const float4 f4 = *reinterpret_cast<const float4*>(Pp + c);
+        const float w = Pc[c - 1], e = Pc[c + 4];
+        const float b0 = c0 * cur.x - rx * (w + cur.y) - ry * (s4.x + n4.x) - rz * (b4.x + f4.x);
+        const float b1 = c0 * cur.y - rx * (cur.x + cur.z) - ry * (s4.y + n4.y) - rz * (b4.y + f4.y);
+        const float b2 = c0 * cur.z - rx * (cur.y + cur.w) - ry * (s4.z + n4.z) - rz * (b4.z + f4.z);
+        const float b3 = c0 * cur.w - rx * (cur.z + e) - ry * (s4.w + n4.w) - rz * (b4.w + f4.w);
+        float4 out;
+        out.x = cur.x + c1 * (cur.x - pv.x) + c2 * (fv.x - b0);
+        out.y = cur.y + c1 * (cur.y - pv.y) + c2 * (fv.y - b1);
+        out.z = cur.z + c1 * (cur.z - pv.z) + c2 * (fv.z - b2);
+        out.w = cur.w + c1 * (cur.w - pv.w) + c2 * (fv.w - b3);
+        if (LAST) {
+          const double2 z01 = make_double2(out.x, out.y), z23 = make_double2(out.z, out.w);
+          double2* zp = reinterpret_cast<double2*>(z + o);
+          zp[0] = z01;
+          zp[1] = z23;
+          const double2* rp = reinterpret_cast<const double2*>(r + o);
+          const double2 r01 = rp[0], r23 = rp[1];
+          acc = fma(r01.x, z01.x, acc);
+          acc = fma(r01.y, z01.y, acc);
+          acc = fma(r23.x, z23.x, acc);
+          acc = fma(r23.y, z23.y, acc);
+        } else {
+          *reinterpret_cast<float4*>(yn + o) = out;
+        }
+      }
+      // every thread is done with the stage of load L-1: refill it two planes ahead
+      __syncthreads();
+      if (L - 1 + CT_ST < nload) {
+        if (tid == 0) {
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          issue(L - 1 + CT_ST);
+        }
+        ++issued;
+      }
+    }
+    if (tm.dead) {
+      if (tid == 0) {
+        atomicExch(ch.err, 1);
+        for (int L = waited; L < issued; ++L) {
+          const unsigned q = gl + L;
+          mbar_wait(&tm.bar[q % CT_ST], (q / CT_ST) & 1u);
+        }
+      }
+      __syncthreads();
+    }
+    tm.gl = gl + nload;
+  }
+  return acc;
+}
+
 // Steps k = 1..m-1 of the vectorised preconditioner: y_1 = f / c is in ring
 // slot 1 (written with f by the pass that updated r), y_k in slot k % 3.
 template <int DIM>
 __device__ __forceinline__ double cheb3_dispatch(const Geom& g, const ChebDev& ch,
                                                  const double* __restrict__ r, int kk, int blk,
-                                                 int nblk) {
+                                                 int nblk, ChebTma& tm) {
   const int sk = kk % 3;
   const float c1 = ch.c1[kk], c2 = ch.c2[kk];
   const float* yk = sk == 0 ? ch.y : sk == 1 ? ch.d0 : ch.d1;
   const float* ykm = sk == 0 ? ch.d1 : sk == 1 ? ch.y : ch.d0;
   float* yn = sk == 0 ? ch.d0 : sk == 1 ? ch.d1 : ch.y;
   const bool last = kk == ch.m - 1;
+  if (DIM == 3 && ch.tmaps) {
+    if (tm.dead) return 0.0;
+    const void* map = ch.tmaps + 128 * sk;
+    if (kk == 1) {
+      if (last) return cheb_tma_step<true, true>(g, ch, map, ykm, ch.res, yn, ch.z, r, c1, c2, blk, nblk, tm);
+      return cheb_tma_step<true, false>(g, ch, map, ykm, ch.res, yn, ch.z, r, c1, c2, blk, nblk, tm);
+    }
+    if (last) return cheb_tma_step<false, true>(g, ch, map, ykm, ch.res, yn, ch.z, r, c1, c2, blk, nblk, tm);
+    return cheb_tma_step<false, false>(g, ch, map, ykm, ch.res, yn, ch.z, r, c1, c2, blk, nblk, tm);
+  }
   if (kk == 1) {
     if (last) return cheb3_step<DIM, true, true>(g, ch, yk, ykm, ch.res, yn, ch.z, r, c1, c2, blk, nblk);
     return cheb3_step<DIM, true, false>(g, ch, yk, ykm, ch.res, yn, ch.z, r, c1, c2, blk, nblk);
@@ -308,7 +464,34 @@ __device__ int pcg_core(const CgDev& a, int nblk, int blk) {
   const long long M = g.M;
   const long long t0 = blk * (long long)blockDim.x + threadIdx.x;
   const long long nt = (long long)nblk * blockDim.x;
-  const GridBarrier bar{};
+  // TMA-fed 3D steps read, through the async proxy, vectors that this kernel
+  // wrote through the generic proxy before a grid barrier: every thread fences
+  // its global writes toward the async proxy before each barrier
+  struct PcgBarrier {
+    bool tma;
+    __device__ void sync() const {
+      if (tma) asm volatile("fence.proxy.async.global;" ::: "memory");
+      cg::this_grid().sync();
+    }
+  };
+  const PcgBarrier bar{ch.tmaps != nullptr};
+  // TMA-fed 3D steps: stage ring and mbarriers in dynamic shared memory
+  extern __shared__ __align__(128) unsigned char cheb_smem[];
+  ChebTma tm{nullptr, nullptr, 0u, false};
+  if (ch.tmaps) {
+    tm.stage = reinterpret_cast<float*>(cheb_smem);
+    tm.bar = reinterpret_cast<unsigned long long*>(cheb_smem + CT_ST * CT_STRIDE * sizeof(float));
+    if (threadIdx.x == 0) {
+      for (int q = 0; q < CT_ST; ++q) mbar_init(&tm.bar[q], 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      // the tensor maps were written to global memory before the launch
+      for (int q = 0; q < 3; ++q)
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(ch.tmaps + 128 * q)
+                     : "memory");
+    }
+    __syncthreads();
+  }
   int parity = 0;
   auto part = [&]() { return ws.part + (size_t)parity * 3 * nblk; };
   double s_rr = 0.0, s_bb = 0.0;
@@ -359,8 +542,8 @@ __device__ int pcg_core(const CgDev& a, int nblk, int blk) {
       const bool last = kk == ch.m - 1;
       double s_rz = 0.0;
       if (ch.vec)
-        s_rz = g.dim == 3 ? cheb3_dispatch<3>(g, ch, ws.r, kk, blk, nblk)
-                          : cheb3_dispatch<2>(g, ch, ws.r, kk, blk, nblk);
+        s_rz = g.dim == 3 ? cheb3_dispatch<3>(g, ch, ws.r, kk, blk, nblk, tm)
+                          : cheb3_dispatch<2>(g, ch, ws.r, kk, blk, nblk, tm);
       else if (last)
         s_rz = cheb_step<true>(g, ch, var, dp, dn, ch.res, ch.y, ch.z, ws.r, c1, c2, blk, nblk);
       else
@@ -414,7 +597,11 @@ __device__ int pcg_core(const CgDev& a, int nblk, int blk) {
       r[1] = (sqrt(r[0]) <= thresh || r[0] == 0.0 || it >= maxit) ? 1.0 : 0.0;
     });
     parity ^= 1;
-    if (o2[1] != 0.0) return it;
+    if (o2[1] != 0.0) {
+      // a block whose TMA wait expired set the error word before the last barrier
+      if (ch.tmaps && *reinterpret_cast<volatile int*>(ch.err) != 0) return -1;
+      return it;
+    }
   }
 }
 
@@ -497,10 +684,10 @@ constexpr long long CG_L2_POINTS = 2LL << 20;  // 5 FP64 vectors of 2 M points =
 constexpr int CG_BIG = PR_CG_BIG_MINB;  // blocks per SM of the instance for grids beyond L2
 
 template <int MINB, int ALG = CG_TEXTBOOK>
-int cg_blocks_of(int num_sms) {
+int cg_blocks_of(int num_sms, size_t dsmem = 0) {
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_kernel<MINB, ALG>, CG_THREADS, 0) !=
-          cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_kernel<MINB, ALG>, CG_THREADS,
+                                                    dsmem) != cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
   if (per_sm > MINB) per_sm = MINB;
@@ -540,6 +727,8 @@ cudaError_t cg_solve(pr_ctx* c, const CgArgs& in) {
     ChebDev& ch = a.ch;
     ch.m = c->opt_g_cheb;
     ch.vec = (c->g.dim >= 2 && !c->var_kappa && c->g.nx % 4 == 0) ? 1 : 0;
+    ch.tmaps = (ch.vec && c->g.dim == 3) ? static_cast<const unsigned char*>(c->cheb_tmaps) : nullptr;
+    ch.err = c->cheb_err;
     ch.lo = c->g_lo;
     ch.hi = c->g_hi;
     // Chebyshev recurrence coefficients on [lo, hi] (centre cc, half width ee)
@@ -573,8 +762,10 @@ cudaError_t cg_solve(pr_ctx* c, const CgArgs& in) {
                   : big ? CG_TEXTBOOK : CG_SINGLE;
   int cap = 0;
   void* fn = nullptr;
+  const size_t dsmem = (alg == CG_CHEB && a.ch.tmaps) ? (size_t)CT_SMEM : 0;
   if (alg == CG_CHEB) {
-    cap = big ? cg_blocks_of<CG_BIG, CG_CHEB>(c->num_sms) : cg_blocks_of<2, CG_CHEB>(c->num_sms);
+    cap = big ? cg_blocks_of<CG_BIG, CG_CHEB>(c->num_sms, dsmem)
+              : cg_blocks_of<2, CG_CHEB>(c->num_sms, dsmem);
     fn = big ? (void*)cg_kernel<CG_BIG, CG_CHEB> : (void*)cg_kernel<2, CG_CHEB>;
   } else if (alg == CG_SINGLE) {
     cap = big ? cg_blocks_of<CG_BIG, CG_SINGLE>(c->num_sms) : cg_blocks_of<2, CG_SINGLE>(c->num_sms);
@@ -590,7 +781,7 @@ cudaError_t cg_solve(pr_ctx* c, const CgArgs& in) {
   if (blocks > c->cg_blocks) blocks = c->cg_blocks;  // partials are sized for cg_blocks
   if (blocks < 1) blocks = 1;
   void* args[] = {&a};
-  return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(CG_THREADS), args, 0, c->stream);
+  return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(CG_THREADS), args, dsmem, c->stream);
 }
 
 namespace {
@@ -682,6 +873,24 @@ cudaError_t cheb_alloc(pr_ctx* c) {
   const Geom& g = c->g;
   cudaError_t e = cudaMalloc(&c->cheb_z, g.M * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&c->cheb_f32, 4 * g.M * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&c->cheb_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->cheb_err, 0, sizeof(int), c->stream);
+  // 3D constant kappa with nx % 4 == 0: tensor maps of the three ring vectors
+  // (y, d0, d1 after the FP32 right-hand side f) for the TMA-fed steps; the
+  // steps fall back to plain vector loads when encoding is not possible
+  if (e == cudaSuccess && g.dim == 3 && !c->var_kappa && g.nx % 4 == 0) {
+    unsigned char maps[3 * 128];
+    bool ok = true;
+    for (int q = 0; q < 3 && ok; ++q)
+      ok = encode_f32_3d_map(maps + 128 * q, c->cheb_f32 + (size_t)(q + 1) * g.M, g.nx, g.ny, g.nz,
+                             CT_PX, CT_PY);
+    if (ok && cudaMalloc(&c->cheb_tmaps, sizeof maps) == cudaSuccess) {
+      e = cudaMemcpyAsync(c->cheb_tmaps, maps, sizeof maps, cudaMemcpyHostToDevice, c->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    } else {
+      cudaGetLastError();  // optional path: no error left behind
+    }
+  }
   if (e == cudaSuccess && c->var_kappa) {
     const long long nfx = (long long)(g.nx + 1) * g.ny * g.nz;
     const long long nfy = g.dim > 1 ? (long long)g.nx * (g.ny + 1) * g.nz : 0;
@@ -705,6 +914,10 @@ cudaError_t cheb_alloc(pr_ctx* c) {
 void cheb_free(pr_ctx* c) {
   if (c->cheb_z) cudaFree(c->cheb_z);
   if (c->cheb_f32) cudaFree(c->cheb_f32);
+  if (c->cheb_tmaps) cudaFree(c->cheb_tmaps);
+  if (c->cheb_err) cudaFree(c->cheb_err);
+  c->cheb_tmaps = nullptr;
+  c->cheb_err = nullptr;
   if (c->gcoef32) cudaFree(c->gcoef32);
   c->cheb_z = nullptr;
   c->cheb_f32 = nullptr;

@@ -165,6 +165,9 @@ int run_sync_pipelined(pr_ctx* c, double* lam, pr_stats* st) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->s_sweep);
   if (e != cudaSuccess) return fail_restore(cuda_fail(c, e, "pipelined predictor"));
   for (int i = 1; i <= N; ++i) {
+    if (iters[i] < 0)
+      return fail_restore(fail(c, PR_ECUDA, "coarse solve: a bounded wait of the TMA-fed "
+                                            "Chebyshev steps expired"));
     S.cg_iterations += iters[i];
     S.coarse_solves += 1;
   }
@@ -241,6 +244,9 @@ int run_sync_pipelined(pr_ctx* c, double* lam, pr_stats* st) {
       maxd = std::max(maxd, d);
     }
     for (int i = k + 2; i <= N; ++i) {
+      if (iters[i] < 0)
+        return fail_restore(fail(c, PR_ECUDA, "coarse solve: a bounded wait of the TMA-fed "
+                                              "Chebyshev steps expired"));
       S.cg_iterations += iters[i];
       S.coarse_solves += 1;
     }

@@ -18,6 +18,7 @@
 #include <cudaTypedefs.h>
 
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace pr {
 
@@ -32,7 +33,6 @@ constexpr unsigned TBYTES = TPLANE * sizeof(float);
 // stage pitch rounded up to 128 bytes, so that every stage starts 128-byte aligned
 constexpr int TSTRIDE = (int)(((TBYTES + 127) / 128) * 128 / sizeof(float));
 constexpr int TMA_THREADS = (TTX / 4) * TTY;  // 256
-constexpr int WAIT_SPINS = 1 << 22;
 
 struct TmaArgs {
   int nx, ny, nz, zchunks;
@@ -41,53 +41,6 @@ struct TmaArgs {
   float* out;
   int* err;
 };
-
-__device__ __forceinline__ unsigned smem_addr(const void* p) {
-  return static_cast<unsigned>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
-               : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
-  unsigned done;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(done)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return done != 0;
-}
-
-// Bounded wait for the completion of phase `parity` of a stage barrier.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
-  for (int i = 0; i < WAIT_SPINS; ++i) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if (i > 32) __nanosleep(64);
-  }
-  return false;
-}
-
-// Tile load of plane (x, y, z, slice) coordinates into shared memory.
-__device__ __forceinline__ void tma_load_plane(float* dst, const CUtensorMap* map, int x, int y,
-                                               int z, int s, unsigned long long* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_addr(dst)),
-      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(s),
-      "r"(smem_addr(bar))
-      : "memory");
-}
 
 __global__ void __launch_bounds__(TMA_THREADS) step3d_tma(const __grid_constant__ CUtensorMap src,
                                                           TmaArgs a) {
@@ -110,7 +63,7 @@ __global__ void __launch_bounds__(TMA_THREADS) step3d_tma(const __grid_constant_
   auto issue = [&](int L) {
     const int s = L % TST;
     mbar_arrive_expect_tx(&bar[s], TBYTES);
-    tma_load_plane(stage[s], &src, x0 - 4, y0 - 1, z0 - 1 + L, slice, &bar[s]);
+    tma_load_4d(stage[s], &src, x0 - 4, y0 - 1, z0 - 1 + L, slice, &bar[s]);
   };
   if (tid == 0)
     for (int L = 0; L < TST && L < nload; ++L) issue(L);
@@ -182,6 +135,27 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 }  // namespace
+
+// Tiled tensor map of a 3D FP32 array (x fastest, then y, then z) with a box of
+// box_x x box_y x 1 elements and zero fill outside the array; false when the
+// driver entry point is missing or the encoding is rejected (base not 16-byte
+// aligned, strides not multiples of 16 bytes, ...).  out receives 128 bytes.
+bool encode_f32_3d_map(void* out, float* base, int nx, int ny, int nz, int box_x, int box_y) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+  const cuuint64_t strides[2] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4};
+  const cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUtensorMap m;
+  if (fn(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
+         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return false;
+  static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
+  memcpy(out, &m, sizeof m);
+  return true;
+}
 
 #ifndef PR_TMA
 #define PR_TMA 1
