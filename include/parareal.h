@@ -273,12 +273,20 @@ int parareal_adjoint_async(pr_ctx* ctx, const pr_event* log_host, size_t n_event
  *    picks single-reduction for grids of at most 2^21 points (their vectors
  *    stay in L2 and the barriers dominate an iteration) and textbook above.
  *    The iterates agree to rounding; the iteration counts to about one. */
+/* and one that changes how the fine steps are grouped into launches (the
+ * arithmetic of every step is the same):
+ *  PR_OPT_F_STEPS_PER_PASS (1 or 2, default 2): the TMA-fed FP32 middle steps
+ *    of the mixed form (3D, kappa = 1, n[0] % 4 == 0) run two steps per pass
+ *    over the state (temporal blocking: one read and one write of the state per
+ *    two steps; the first step's values on the halo the second needs are
+ *    recomputed per tile) or one.  Results are bitwise identical. */
 enum pr_option {
   PR_OPT_PIPELINE = 1,
   PR_OPT_PIPELINE_CHUNKS = 2,
   PR_OPT_CG_BLOCKS_PER_SM = 3,
   PR_OPT_G_CHEBYSHEV = 4,
-  PR_OPT_G_CG = 5
+  PR_OPT_G_CG = 5,
+  PR_OPT_F_STEPS_PER_PASS = 6
 };
 int parareal_set_option(pr_ctx* ctx, int option, double value);
 

@@ -18,6 +18,7 @@ PR_EXPLICIT_EULER, PR_IMPLICIT_EULER, PR_CRANK_NICOLSON = 0, 1, 2
 PR_SOLVER_THOMAS, PR_SOLVER_CG = 0, 1
 PR_OPT_PIPELINE, PR_OPT_PIPELINE_CHUNKS, PR_OPT_CG_BLOCKS_PER_SM, PR_OPT_G_CHEBYSHEV = 1, 2, 3, 4
 PR_OPT_G_CG = 5
+PR_OPT_F_STEPS_PER_PASS = 6
 
 
 class pr_problem(C.Structure):

@@ -416,7 +416,7 @@ int parareal_serial_fine(pr_ctx* c, double* lam, pr_stats* st) {
     st->t_total_ms = ms;
     st->t_fine_ms = ms;
     st->fine_lups = (long long)c->prob.N * M * c->prob.f_steps;
-    st->launches = (long long)c->prob.N * (c->prob.f_scheme == PR_EXPLICIT_EULER ? c->prob.f_steps : 1);
+    st->launches = (long long)c->prob.N * fine_launch_count(c);
     st->fine_cg_iterations = (long long)cn_take_iterations(c);
     st->iterations = 0;
     st->converged = 1;
@@ -451,6 +451,11 @@ int parareal_set_option(pr_ctx* c, int option, double value) {
           return cuda_fail(c, e, "Chebyshev workspaces");
         }
       }
+      return PR_OK;
+    case PR_OPT_F_STEPS_PER_PASS:
+      if (!(value == 1.0 || value == 2.0))
+        return fail(c, PR_EINVAL, "fine steps per pass must be 1 or 2");
+      c->opt_f_blocking = (int)value;
       return PR_OK;
     case PR_OPT_G_CG:
       if (!(value == 0.0 || value == 1.0 || value == 2.0))
@@ -532,7 +537,7 @@ int parareal_run_sync(pr_ctx* c, double* lam, pr_stats* st) {
     }
     PR_CUDA(c, cudaEventRecord(c->ev[3], c->stream));
     nvtxRangePushA("coarse sweep");
-    S.launches += p.f_scheme == PR_EXPLICIT_EULER ? p.f_steps : 1;
+    S.launches += fine_launch_count(c);
     S.fine_lups += (long long)count * M * p.f_steps;
     // sequential coarse sweep with the fused correction and increment
     PR_CUDA(c, cudaMemsetAsync(c->delta_dev, 0, N * sizeof(unsigned long long), c->stream));

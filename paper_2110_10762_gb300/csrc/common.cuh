@@ -93,6 +93,8 @@ struct pr_ctx {
   // TMA-fed FP32 3D steps (tma_stencil.cu): tensor maps of f32a / f32b
   bool tma_ok = false;
   alignas(64) unsigned char tma_map[2][128] = {};
+  alignas(64) unsigned char tma_map2[2][128] = {};  // same buffers, box for two steps per pass
+  int opt_f_blocking = 2;    // FP32 TMA fine steps per pass (1 or 2; PR_OPT_F_STEPS_PER_PASS)
   int* tma_err = nullptr;
   double* cg_x = nullptr;    // CG vectors (M each)
   double* cg_r = nullptr;
@@ -193,6 +195,8 @@ cudaError_t fine_apply(pr_ctx* c, const double* in, double* out, int count);
 bool tma_prepare(pr_ctx* c);
 bool encode_f32_3d_map(void* out, float* base, int nx, int ny, int nz, int box_x, int box_y);
 cudaError_t tma_step(pr_ctx* c, const float* src, float* dst, int count);
+cudaError_t tma_step2(pr_ctx* c, const float* src, float* dst, int count);
+int fine_launch_count(const pr_ctx* c);
 int tma_take_error(pr_ctx* c);
 
 // ---- tridiagonal partition solver (tridiag.cu)

@@ -101,7 +101,7 @@ int run_sync_pipelined(pr_ctx* c, double* lam, pr_stats* st) {
       if (e == cudaSuccess) e = cudaEventRecord(evT1(par, ch), c->s_fine);
       if (e == cudaSuccess) e = cudaEventRecord(evF(par, ch), c->s_fine);
       if (e != cudaSuccess) return cuda_fail(c, e, "pipelined fine chunk");
-      S.launches += p.f_scheme == PR_EXPLICIT_EULER ? p.f_steps : 1;
+      S.launches += fine_launch_count(c);
       b.lups += (long long)(chunk_hi(b.kk, ch) - chunk_lo(b.kk, ch)) * M * p.f_steps;
       ++b.next;
     }

@@ -456,6 +456,19 @@ cudaError_t explicit_step64(pr_ctx* c, const double* in, double* out, int count)
   return launch_step<double, double, double>(c, in, out, count, c->fvar);
 }
 
+// Kernel launches of one batched F (the dispatch below): one per fine step,
+// except the TMA-fed FP32 middle steps, which run two per launch when enabled.
+int fine_launch_count(const pr_ctx* c) {
+  const pr_problem& p = c->prob;
+  if (p.f_scheme != PR_EXPLICIT_EULER) return 1;
+  const int steps = p.f_steps;
+  if (p.f_prec == 32 && c->tma_ok && c->opt_f_blocking == 2 && steps > 3) {
+    const int mid = steps - 2;
+    return 2 + mid / 2 + mid % 2;
+  }
+  return steps;
+}
+
 cudaError_t explicit_fine(pr_ctx* c, const double* in, double* out, int count, int steps,
                           int prec) {
   if (count <= 0 || steps <= 0) return cudaSuccess;
@@ -477,11 +490,15 @@ cudaError_t explicit_fine(pr_ctx* c, const double* in, double* out, int count, i
   e = launch_step<double, float, float>(c, in, c->f32a, count, c->fvar32);
   if (e != cudaSuccess) return e;
   const float* src = c->f32a;
-  for (int s = 1; s < steps - 1; ++s) {
+  for (int s = 1; s < steps - 1;) {
     float* dst = (src == c->f32a) ? c->f32b : c->f32a;
-    e = c->tma_ok ? tma_step(c, src, dst, count)
-                  : launch_step<float, float, float>(c, src, dst, count, c->fvar32);
+    // TMA path: two middle steps per pass where two remain (temporal blocking)
+    const bool two = c->tma_ok && c->opt_f_blocking == 2 && s + 1 < steps - 1;
+    e = two ? tma_step2(c, src, dst, count)
+        : c->tma_ok ? tma_step(c, src, dst, count)
+                    : launch_step<float, float, float>(c, src, dst, count, c->fvar32);
     if (e != cudaSuccess) return e;
+    s += two ? 2 : 1;
     src = dst;
   }
   e = launch_step<float, double, float>(c, src, out, count, c->fvar32);

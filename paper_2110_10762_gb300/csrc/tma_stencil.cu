@@ -42,7 +42,25 @@ struct TmaArgs {
   int* err;
 };
 
-__global__ void __launch_bounds__(TMA_THREADS) step3d_tma(const __grid_constant__ CUtensorMap src,
+// One explicit step at four consecutive x points, written with explicit FMAs in
+// a fixed order so that the one-step and two-step kernels round identically:
+// u' = c0 u + rx (w + e) + ry (s + n) + rz (b + f).
+__device__ __forceinline__ float step1(float c0, float rx, float ry, float rz, float u, float w,
+                                       float e, float sn, float bf) {
+  return fmaf(rz, bf, fmaf(ry, sn, fmaf(rx, w + e, c0 * u)));
+}
+
+__device__ __forceinline__ float4 step4(float c0, float rx, float ry, float rz, float4 cur, float w,
+                                        float e, float4 s4, float4 n4, float4 b4, float4 f4) {
+  float4 r;
+  r.x = step1(c0, rx, ry, rz, cur.x, w, cur.y, s4.x + n4.x, b4.x + f4.x);
+  r.y = step1(c0, rx, ry, rz, cur.y, cur.x, cur.z, s4.y + n4.y, b4.y + f4.y);
+  r.z = step1(c0, rx, ry, rz, cur.z, cur.y, cur.w, s4.z + n4.z, b4.z + f4.z);
+  r.w = step1(c0, rx, ry, rz, cur.w, cur.z, e, s4.w + n4.w, b4.w + f4.w);
+  return r;
+}
+
+__global__ void __launch_bounds__(TMA_THREADS, 4) step3d_tma(const __grid_constant__ CUtensorMap src,
                                                           TmaArgs a) {
   __shared__ __align__(128) float stage[TST][TSTRIDE];
   __shared__ __align__(8) unsigned long long bar[TST];
@@ -96,11 +114,7 @@ __global__ void __launch_bounds__(TMA_THREADS) step3d_tma(const __grid_constant_
       const float4 b4 = *reinterpret_cast<const float4*>(Pm + c);
       const float4 f4 = *reinterpret_cast<const float4*>(Pp + c);
       const float w = Pc[c - 1], e = Pc[c + 4];
-      float4 r;
-      r.x = c0 * cur.x + rx * (w + cur.y) + ry * (s4.x + n4.x) + rz * (b4.x + f4.x);
-      r.y = c0 * cur.y + rx * (cur.x + cur.z) + ry * (s4.y + n4.y) + rz * (b4.y + f4.y);
-      r.z = c0 * cur.z + rx * (cur.y + cur.w) + ry * (s4.z + n4.z) + rz * (b4.z + f4.z);
-      r.w = c0 * cur.w + rx * (cur.z + e) + ry * (s4.w + n4.w) + rz * (b4.w + f4.w);
+      const float4 r = step4(c0, rx, ry, rz, cur, w, e, s4, n4, b4, f4);
       *reinterpret_cast<float4*>(out + zi * plane + (long long)gy * a.nx + gx) = r;
     }
     // every thread is done with the stage of load L-1: refill it two planes ahead
@@ -117,6 +131,168 @@ __global__ void __launch_bounds__(TMA_THREADS) step3d_tma(const __grid_constant_
     atomicExch(a.err, 1);
     // wait (bounded) for this block's own loads still in flight before exiting,
     // so that no copy lands in shared memory after the block has left
+    for (int L = waited; L < issued; ++L) mbar_wait(&bar[L % TST], (L / TST) & 1);
+  }
+}
+
+// ---- two fine steps per pass (temporal blocking).  The block owns the same
+// 64 x 16 output column and streams z; input planes come in with a 2-point halo
+// (72 x 20 floats, the x halo 4 wide for alignment) through the same kind of
+// mbarrier ring.  Per plane j: the first step is computed on the 72 x 18 region
+// the second step needs (324 float4 items over 256 threads) into a three-plane
+// shared ring S1, with every value outside the grid set to the Dirichlet zero;
+// then the second step of plane j - 1 is computed from S1 and stored.  Each
+// thread carries the z-neighbours of its own items in registers (the previous
+// and current plane of its input column, and of its first-step column), so a
+// plane costs one block barrier, and shared memory is read only for in-plane
+// neighbours.  Ring reuse: S1 slot (j + 1) % 3 is written while slots j % 3 and
+// (j - 1) % 3 are read, and the input stage of plane j is refilled after the
+// barrier that ends its last use.  HBM traffic: one read and one write of the
+// state per two steps.
+constexpr int T2Y = TTY + 4;                    // staged input rows (halo 2)
+constexpr unsigned T2BYTES = TPX * T2Y * sizeof(float);
+constexpr int T2STRIDE = (int)(((T2BYTES + 127) / 128) * 128 / sizeof(float));
+constexpr int S1Y = TTY + 2;                    // first-step rows
+constexpr int S1PLANE = TPX * S1Y;              // 72 x 18
+constexpr int T2ITEMS = (TPX / 4) * S1Y;        // 324 float4 items of the first step
+
+__global__ void __launch_bounds__(TMA_THREADS, 2) step3d_tma2(const __grid_constant__ CUtensorMap src,
+                                                           TmaArgs a) {
+  __shared__ __align__(128) float stage[TST][T2STRIDE];
+  __shared__ __align__(16) float s1[3][S1PLANE];
+  __shared__ __align__(8) unsigned long long bar[TST];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int slice = blockIdx.z / a.zchunks;
+  const int z0 = (blockIdx.z - slice * a.zchunks) * TZC;
+  const int zend = min(z0 + TZC, a.nz);
+  const int nload = zend - z0 + 4;  // input planes z0-2 .. zend+1; load L = plane - (z0-2)
+  const int x0 = blockIdx.x * TTX, y0 = blockIdx.y * TTY;
+  if (tid == 0) {
+#pragma unroll
+    for (int q = 0; q < TST; ++q) mbar_init(&bar[q], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](int L) {
+    const int q = L % TST;
+    mbar_arrive_expect_tx(&bar[q], T2BYTES);
+    tma_load_4d(stage[q], &src, x0 - 4, y0 - 2, z0 - 2 + L, slice, &bar[q]);
+  };
+  if (tid == 0)
+    for (int L = 0; L < TST && L < nload; ++L) issue(L);
+  int issued = TST < nload ? TST : nload;
+  int waited = 0;
+  bool ok = true, aborted = false;
+  auto wait_upto = [&](int L) {  // loads 0..L complete
+    while (ok && waited <= L) {
+      ok = mbar_wait(&bar[waited % TST], (waited / TST) & 1);
+      if (ok) ++waited;
+    }
+  };
+  const float c0 = a.c0, rx = a.rx, ry = a.ry, rz = a.rz;
+  const long long plane = (long long)a.nx * a.ny;
+  float* out = a.out + (long long)slice * a.M;
+  // first-step items of this thread: item i -> row r = i / 18, float4 column q = i % 18
+  // (grid x = x0 - 4 + 4 q, y = y0 - 1 + r; stage row r + 1, column 4 q)
+  const int nitem = tid + TMA_THREADS < T2ITEMS ? 2 : 1;
+  int ir[2], iq[2];
+  bool ixy[2];
+  float4 in_prev[2], in_cur[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int i = tid + k * TMA_THREADS;
+    ir[k] = i / (TPX / 4);
+    iq[k] = i % (TPX / 4);
+    const int gx1 = x0 - 4 + 4 * iq[k], gy1 = y0 - 1 + ir[k];
+    ixy[k] = k < nitem && gx1 >= 0 && gx1 < a.nx && gy1 >= 0 && gy1 < a.ny;
+    in_prev[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    in_cur[k] = in_prev[k];
+  }
+  // second-step point of this thread
+  const int gx = x0 + 4 * tx, gy = y0 + ty;
+  const bool inside = gx < a.nx && gy < a.ny;
+  const int c2 = (ty + 1) * TPX + 4 + 4 * tx;  // its first point in an S1 plane
+  float4 s1_prev = make_float4(0.f, 0.f, 0.f, 0.f), s1_cur = s1_prev;
+  // prologue: own input columns of planes z0-2 and z0-1
+  wait_upto(1);
+  if (!__syncthreads_or(!ok)) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+      if (k < nitem) {
+        const int o = (ir[k] + 1) * TPX + 4 * iq[k];
+        in_prev[k] = *reinterpret_cast<const float4*>(stage[0] + o);
+        in_cur[k] = *reinterpret_cast<const float4*>(stage[1] + o);
+      }
+  } else {
+    aborted = true;
+  }
+  __syncthreads();
+  if (!aborted && TST < nload) {   // the stage of load 0 is free: refill it
+    if (tid == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(TST);
+    }
+    ++issued;
+  }
+  for (int j = z0 - 1; j <= zend && !aborted; ++j) {
+    const int Lj = j - z0 + 2;  // load index of input plane j
+    wait_upto(Lj + 1);
+    if (__syncthreads_or(!ok)) {
+      aborted = true;
+      break;
+    }
+    // (b) first step at plane j into S1[(j + 3) % 3]
+    {
+      const float* Pc = stage[Lj % TST];
+      const float* Pn = stage[(Lj + 1) % TST];
+      float* S = s1[(j + 3) % 3];
+      const bool zin = j >= 0 && j < a.nz;
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        if (k >= nitem) break;
+        const int o = (ir[k] + 1) * TPX + 4 * iq[k];
+        const float4 nx4 = *reinterpret_cast<const float4*>(Pn + o);
+        const float4 cur = in_cur[k];
+        const float4 s4 = *reinterpret_cast<const float4*>(Pc + o - TPX);
+        const float4 n4 = *reinterpret_cast<const float4*>(Pc + o + TPX);
+        const float w = iq[k] > 0 ? Pc[o - 1] : 0.f;
+        const float e = iq[k] < TPX / 4 - 1 ? Pc[o + 4] : 0.f;
+        const float4 b4 = in_prev[k];
+        float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (zin && ixy[k]) r = step4(c0, rx, ry, rz, cur, w, e, s4, n4, b4, nx4);
+        *reinterpret_cast<float4*>(S + ir[k] * TPX + 4 * iq[k]) = r;
+        in_prev[k] = cur;
+        in_cur[k] = nx4;
+      }
+    }
+    // (c) S1 plane j complete; the input stage of plane j has had its last use
+    __syncthreads();
+    if (Lj + TST < nload) {
+      if (tid == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue(Lj + TST);
+      }
+      ++issued;
+    }
+    // (d) second step at plane j - 1 from S1 planes j - 2, j - 1 (registers) and j
+    const float4 s1_next = *reinterpret_cast<const float4*>(s1[(j + 3) % 3] + c2);
+    const int zo = j - 1;
+    if (zo >= z0 && zo < zend && inside) {
+      const float* Q = s1[(j + 2) % 3];   // plane j - 1
+      const float4 cur = s1_cur;
+      const float4 s4 = *reinterpret_cast<const float4*>(Q + c2 - TPX);
+      const float4 n4 = *reinterpret_cast<const float4*>(Q + c2 + TPX);
+      const float w = Q[c2 - 1], e = Q[c2 + 4];
+      const float4 r = step4(c0, rx, ry, rz, cur, w, e, s4, n4, s1_prev, s1_next);
+      *reinterpret_cast<float4*>(out + zo * plane + (long long)gy * a.nx + gx) = r;
+    }
+    s1_prev = s1_cur;
+    s1_cur = s1_next;
+  }
+  if (aborted && tid == 0) {
+    atomicExch(a.err, 1);
     for (int L = waited; L < issued; ++L) mbar_wait(&bar[L % TST], (L / TST) & 1);
   }
 }
@@ -178,15 +354,21 @@ bool tma_prepare(pr_ctx* c) {
   const cuuint64_t strides[3] = {(cuuint64_t)g.nx * 4, (cuuint64_t)g.nx * g.ny * 4,
                                  (cuuint64_t)g.M * 4};
   const cuuint32_t box[4] = {TPX, TPY, 1, 1};
+  const cuuint32_t box2[4] = {TPX, T2Y, 1, 1};   // two steps per pass: 2-point halo
   const cuuint32_t estr[4] = {1, 1, 1, 1};
   float* bufs[2] = {c->f32a, c->f32b};
   for (int i = 0; i < 2; ++i) {
-    CUtensorMap m;
+    CUtensorMap m, m2;
     if (fn(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, bufs[i], dims, strides, box, estr,
            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return false;
+    if (fn(&m2, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, bufs[i], dims, strides, box2, estr,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
     memcpy(c->tma_map[i], &m, sizeof m);
+    memcpy(c->tma_map2[i], &m2, sizeof m2);
   }
   if (cudaMalloc(&c->tma_err, sizeof(int)) != cudaSuccess ||
       cudaMemsetAsync(c->tma_err, 0, sizeof(int), c->stream) != cudaSuccess) {
@@ -220,6 +402,30 @@ cudaError_t tma_step(pr_ctx* c, const float* src, float* dst, int count) {
   a.err = c->tma_err;
   dim3 grd((g.nx + TTX - 1) / TTX, (g.ny + TTY - 1) / TTY, count * a.zchunks);
   step3d_tma<<<grd, TMA_THREADS, 0, c->stream>>>(m, a);
+  return cudaGetLastError();
+}
+
+// Two FP32 steps from one ping-pong buffer to the other in one pass (temporal
+// blocking; src must be f32a or f32b).
+cudaError_t tma_step2(pr_ctx* c, const float* src, float* dst, int count) {
+  const Geom& g = c->g;
+  const int which = src == c->f32a ? 0 : 1;
+  CUtensorMap m;
+  memcpy(&m, c->tma_map2[which], sizeof m);
+  TmaArgs a{};
+  a.nx = g.nx;
+  a.ny = g.ny;
+  a.nz = g.nz;
+  a.zchunks = (g.nz + TZC - 1) / TZC;
+  a.M = g.M;
+  a.c0 = static_cast<float>(c->fst.c0);
+  a.rx = static_cast<float>(c->fst.rx);
+  a.ry = static_cast<float>(c->fst.ry);
+  a.rz = static_cast<float>(c->fst.rz);
+  a.out = dst;
+  a.err = c->tma_err;
+  dim3 grd((g.nx + TTX - 1) / TTX, (g.ny + TTY - 1) / TTY, count * a.zchunks);
+  step3d_tma2<<<grd, TMA_THREADS, 0, c->stream>>>(m, a);
   return cudaGetLastError();
 }
 

@@ -103,6 +103,39 @@ def test_fine_fp32_vectorized_3d(n, var):
         assert 1e-12 < err < MIXED_TOL, (s, err)
 
 
+@pytest.mark.parametrize("n,f_steps", [((68, 19, 70), 3), ((68, 19, 70), 4), ((64, 17, 33), 5),
+                                        ((132, 9, 37), 8), ((8, 5, 3), 9), ((64, 16, 32), 6)])
+def test_fine_fp32_two_steps_per_pass(n, f_steps):
+    """TMA-fed FP32 middle steps two per pass (temporal blocking) against one per
+    pass: bitwise identical (the same FMA-ordered step, the first step's values on
+    the halo recomputed per tile and set to the Dirichlet zero outside the grid),
+    and against the FP64 oracle.  Odd and even middle-step counts (a single step
+    finishes an odd count), ragged x/y tiles and z chunks, a grid smaller than one
+    tile."""
+    rng = np.random.default_rng(19)
+    h = tuple(1.0 / (m + 1) for m in n)
+    shape = tuple(reversed(n))
+    p = dict(dim=3, n=n, h=h, N=3, f_steps=f_steps, dt=0.15 * min(h) ** 2, f_scheme="explicit",
+             g_solver="cg", g_rtol=1e-10, f_prec=32, kappa=None, u0=rng.standard_normal(shape),
+             tol=0.0)
+    P = oracle_props(p)
+    X = rng.standard_normal((3,) + shape)
+    got = {}
+    with Ctx(p) as c:
+        xin = dev(X)
+        for per_pass in (1, 2):
+            pr.parareal_set_option(c.ctx, pr.PR_OPT_F_STEPS_PER_PASS, per_pass)
+            out = torch().empty_like(xin)
+            pr.parareal_fine(c.ctx, xin, out, 3)
+            got[per_pass] = host(out).reshape(X.shape)
+        with pytest.raises(pr.PararealError):
+            pr.parareal_set_option(c.ctx, pr.PR_OPT_F_STEPS_PER_PASS, 3)
+    assert np.array_equal(got[1], got[2])
+    for s in range(3):
+        err = rel_l2(got[2][s], P.F(X[s]))
+        assert 1e-12 < err < MIXED_TOL, (s, err)
+
+
 @pytest.mark.parametrize("n,f_steps", [((37, 19, 70), 2), ((37, 19, 70), 7), ((64, 8, 33), 4),
                                         ((5, 3, 2), 3), ((33, 9, 97), 6)])
 def test_fine_fp32_3d_ragged_chunks_and_step_counts(n, f_steps):
