@@ -88,11 +88,8 @@ CN_OPS_PER_LUP = {2: 13, 3: 17}
 NOMINAL_FP64_OPS = 625.0  # G FP64-pipe ops/s: 1.25 TFLOP/s nominal / 2 flops per DFMA
 # DRAM bytes (read + write) per cell update of the dominant kernel, from one ncu capture
 # of the current kernel; None where no capture of the current kernel exists.
-# (profiles/step2d_fp64_heat2d_1024x1024.md: 1016.3 MB for 63 x 1048576 updates;
-# profiles/step3d_tma_fp32_heat3d_160cubed.md: 493.6 MB for 15 x 160^3 updates, a
-# smaller case of the same kernel whose traffic grows in proportion to the updates).
-NCU_TRAFFIC_PER_LUP = {"heat2d_explicit": 1016.3e6 / (63 * 1048576),
-                       "heat3d_mixed": 493.6e6 / (15 * 160 ** 3)}
+# (profiles/step2d_fp64_heat2d_1024x1024.md: 1016.3 MB for 63 x 1048576 updates.)
+NCU_TRAFFIC_PER_LUP = {"heat2d_explicit": 1016.3e6 / (63 * 1048576)}
 
 
 def cost_model_sync(p, st, ms_per_solve):
@@ -188,6 +185,8 @@ def parse():
     ap.add_argument("--g-cheb", type=int, default=None,
                     help="coarse CG preconditioned by this many FP32 Chebyshev steps (0 = plain "
                          "CG; default: the workload's setting)")
+    ap.add_argument("--f-per-pass", type=int, default=2, choices=[1, 2],
+                    help="TMA-fed FP32 fine steps per pass over the state (temporal blocking)")
     ap.add_argument("--g-cg", type=int, default=0, choices=[0, 1, 2],
                     help="unpreconditioned coarse CG recurrence: 0 automatic, 1 textbook, "
                          "2 single-reduction")
@@ -841,6 +840,7 @@ def run_ours(args, world, rank, local):
         pr.parareal_set_option(ctx, pr.PR_OPT_PIPELINE_CHUNKS, args.chunks)
         pr.parareal_set_option(ctx, pr.PR_OPT_CG_BLOCKS_PER_SM, args.cg_bps)
     apply_coarse_options(pr, ctx, args)
+    pr.parareal_set_option(ctx, pr.PR_OPT_F_STEPS_PER_PASS, args.f_per_pass)
     lam = torch.empty((N + 1) * M, dtype=torch.float64, device="cuda")
     if args.profile:
         code, st = pr.parareal_run_sync(ctx, lam)
@@ -915,11 +915,26 @@ def run_ours(args, world, rank, local):
         return r
 
     if is_mixed:
+        tma = dim == 3 and p["n"][0] % 4 == 0 and p.get("kappa") is None
+        nf = p["f_steps"]
+        # passes of one F: the first (FP64 in, FP32 out: 12 B per point) and the last
+        # (FP32 in, FP64 out: 12 B), the middle steps one per pass or, TMA-fed, two per
+        # pass (one read and one write of the FP32 state, 8 B per point per pass)
+        if nf == 1:
+            passes, bytes_pt = 1, 16
+        else:
+            mid = nf - 2
+            mid_passes = (mid // 2 + mid % 2) if (tma and args.f_per_pass == 2) else mid
+            passes, bytes_pt = 2 + mid_passes, 24 + 8 * mid_passes
+        fine_launches = sum(s["iterations"] for s in roof_stats) * passes
+        alg_bytes = bytes_pt * lups_r / nf
         roof = {"bound": "hbm", "achieved": alg_bytes / (t_fine / 1e3) / 1e9, "peak": hbm_peak,
                 "unit": "GB/s", "traffic": None,
-                "kernel": ("step3d_tma (TMA-fed FP32 steps; first/last step step3d_v4)"
-                           if p["n"][0] % 4 == 0 and p.get("kappa") is None else "step3d_v4<float>"),
-                "peak_kind": peak_kind}
+                "kernel": (("step3d_tma2 (two TMA-fed FP32 steps per pass" if args.f_per_pass == 2
+                            else "step3d_tma (TMA-fed FP32 steps") +
+                           "; first/last step step3d_v4 with FP64 I/O)" if tma else "step3d_v4<float>"),
+                "peak_kind": peak_kind,
+                "bytes_per_lup": bytes_pt / nf, "passes_per_F": passes}
         roof["frac"] = roof["achieved"] / roof["peak"]
     elif is_cn:
         f_its = sum(s["fine_cg_iterations"] for s in roof_stats)
@@ -944,7 +959,8 @@ def run_ours(args, world, rank, local):
                                       "frac": alg_bytes / (t_fine / 1e3) / 1e9 / hbm_peak}})
     roof["avg_launch_ms"] = t_fine / max(fine_launches, 1)
     lups_per_launch = lups_r / max(fine_launches, 1)
-    roof["algorithmic_bytes_per_launch"] = 2 * b_elem * lups_per_launch
+    roof["algorithmic_bytes_per_launch"] = (alg_bytes / max(fine_launches, 1) if is_mixed
+                                            else 2 * b_elem * lups_per_launch)
     tpl = NCU_TRAFFIC_PER_LUP.get(args.workload)
     roof["traffic"] = tpl * lups_per_launch if tpl else None
     # coarse sweep (the predictor and the corrections' CG solves): FP64 pipe
