@@ -449,6 +449,190 @@ __device__ __forceinline__ double cheb3_dispatch(const Geom& g, const ChebDev& c
   return cheb3_step<DIM, false, false>(g, ch, yk, ykm, ch.res, yn, ch.z, r, c1, c2, blk, nblk);
 }
 
+// ---- vectorised FP64 passes of the preconditioned CG (constant kappa, dim >= 2,
+// nx % 4 == 0).  A warp owns 64 consecutive x (one double2 per lane) of one row
+// of the middle axis (y in 3D) and streams CV_ZC planes of the slowest axis,
+// carrying the previous, current and next plane of the stencil operand in
+// registers; x-neighbours come by shuffles (the warp's edge values by one load
+// each), middle-axis neighbours by double2 loads.  fn(o, cur, w, e, mid, bf) is
+// called for every lane that owns points: o = offset of its first point, cur =
+// its two values, w / e = the west neighbour of the first and the east
+// neighbour of the second, mid = the sum of the middle-axis neighbours (3D), bf
+// = the sum of the streamed-axis neighbours.
+template <int DIM, class Fn>
+__device__ __forceinline__ void stream64(const Geom& g, const double* __restrict__ u, int blk,
+                                         int nblk, Fn&& fn) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  const long long gw = (long long)blk * wpb + (threadIdx.x >> 5);
+  const long long nw = (long long)nblk * wpb;
+  const int nx = g.nx;
+  const int ns = DIM == 3 ? g.nz : g.ny;
+  const int nm = DIM == 3 ? g.ny : 1;
+  const long long sst = DIM == 3 ? (long long)g.nx * g.ny : (long long)g.nx;
+  const int XC = (nx + 63) >> 6;
+  const int SC = (ns + CV_ZC - 1) / CV_ZC;
+  const long long items = (long long)XC * nm * SC;
+  const double2 zero = make_double2(0.0, 0.0);
+  for (long long j = gw; j < items; j += nw) {
+    const int xc = (int)(j % XC);
+    const long long t = j / XC;
+    const int ym = (int)(t % nm);
+    const int s0 = (int)(t / nm) * CV_ZC;
+    const int s1 = min(s0 + CV_ZC, ns);
+    const int x = xc * 64 + 2 * lane;
+    const bool act = x < nx;
+    const long long row = (DIM == 3 ? (long long)ym * nx : 0) + x;
+    double2 prv = zero, cur = zero;
+    if (act) {
+      if (s0 > 0) prv = *reinterpret_cast<const double2*>(u + (s0 - 1) * sst + row);
+      cur = *reinterpret_cast<const double2*>(u + s0 * sst + row);
+    }
+    for (int sl = s0; sl < s1; ++sl) {
+      const long long o = sl * sst + row;
+      double2 nxt = zero, mid = zero;
+      double wv = 0.0, ev = 0.0;
+      if (act) {
+        if (sl + 1 < ns) nxt = *reinterpret_cast<const double2*>(u + o + sst);
+        if (DIM == 3) {
+          if (ym > 0) mid = *reinterpret_cast<const double2*>(u + o - nx);
+          if (ym + 1 < nm) {
+            const double2 q = *reinterpret_cast<const double2*>(u + o + nx);
+            mid.x += q.x;
+            mid.y += q.y;
+          }
+        }
+        if (lane == 0 && x > 0) wv = u[o - 1];
+        if (lane == 31 && x + 2 < nx) ev = u[o + 2];
+      }
+      const double wsh = __shfl_up_sync(FULL, cur.y, 1);
+      const double esh = __shfl_down_sync(FULL, cur.x, 1);
+      if (lane > 0) wv = wsh;
+      if (lane < 31) ev = esh;
+      if (act) fn(o, cur, wv, ev, mid, make_double2(prv.x + nxt.x, prv.y + nxt.y));
+      prv = cur;
+      cur = nxt;
+    }
+  }
+}
+
+// Scaled coarse operator B' u = (I + dT A) u / R_x at one point (constant kappa):
+// c0' u - (w + e) - R_y' (s + n) - R_z' (b + f), with the same operation order as
+// op_point.  In 2D the middle-axis sum is absent and the streamed axis is y.
+template <int DIM>
+__device__ __forceinline__ double bop(const StencilConst& ks, double u, double w, double e,
+                                      double mid, double bf) {
+  double r = fma(ks.c0, u, -(w + e));
+  if (DIM == 3) {
+    r = fma(-ks.ry, mid, r);
+    r = fma(-ks.rz, bf, r);
+  } else {
+    r = fma(-ks.ry, bf, r);
+  }
+  return r;
+}
+
+// Unscaled (I + dT A) u at one point, the operation order of gop_xyz.
+template <int DIM>
+__device__ __forceinline__ double gop_pt(const StencilConst& k, double u, double w, double e,
+                                         double mid, double bf) {
+  double r = k.c0 * u - k.rx * (w + e);
+  if (DIM == 3) {
+    r -= k.ry * mid;
+    r -= k.rz * bf;
+  } else {
+    r -= k.ry * bf;
+  }
+  return r;
+}
+
+// Start of the preconditioned CG on the vectorised path: r = b - B x0, x = x0,
+// f = FP32(r), y_1 = f / c (ring slot 1); returns the partial r.r and b.b.
+template <int DIM>
+__device__ __forceinline__ void pcg_setup_vec(const CgDev& a, double& rr, double& bb, int blk,
+                                              int nblk) {
+  const CgWork& ws = a.ws;
+  const ChebDev& ch = a.ch;
+  const StencilConst k = a.k;
+  double srr = 0.0, sbb = 0.0;
+  stream64<DIM>(a.g, a.x0, blk, nblk,
+                [&](long long o, double2 c, double w, double e, double2 mid, double2 bf) {
+                  const double2 b = *reinterpret_cast<const double2*>(a.b + o);
+                  const double r0 = b.x - gop_pt<DIM>(k, c.x, w, c.y, mid.x, bf.x);
+                  const double r1 = b.y - gop_pt<DIM>(k, c.y, c.x, e, mid.y, bf.y);
+                  *reinterpret_cast<double2*>(ws.x + o) = c;
+                  *reinterpret_cast<double2*>(ws.r + o) = make_double2(r0, r1);
+                  const float f0 = static_cast<float>(r0), f1 = static_cast<float>(r1);
+                  *reinterpret_cast<float2*>(ch.res + o) = make_float2(f0, f1);
+                  *reinterpret_cast<float2*>(ch.d0 + o) = make_float2(f0 * ch.inv_c, f1 * ch.inv_c);
+                  srr = fma(r0, r0, fma(r1, r1, srr));
+                  sbb = fma(b.x, b.x, fma(b.y, b.y, sbb));
+                });
+  rr = srr;
+  bb = sbb;
+}
+
+// Direction update fused with the operator on the vectorised path:
+//   p = z + beta p,   q = B' z + beta q   (= B' p, the operator being linear),
+// one pass over z (with its stencil), p and q; returns the partial p.q.  On the
+// first iteration p = z and q = B' z.
+template <int DIM>
+__device__ __forceinline__ double pcg_pq_vec(const CgDev& a, const StencilConst& ks, double beta,
+                                             bool first, int blk, int nblk) {
+  const CgWork& ws = a.ws;
+  double acc = 0.0;
+  stream64<DIM>(a.g, a.ch.z, blk, nblk,
+                [&](long long o, double2 c, double w, double e, double2 mid, double2 bf) {
+                  const double q0 = bop<DIM>(ks, c.x, w, c.y, mid.x, bf.x);
+                  const double q1 = bop<DIM>(ks, c.y, c.x, e, mid.y, bf.y);
+                  double2 pn = c, qn = make_double2(q0, q1);
+                  if (!first) {
+                    const double2 po = *reinterpret_cast<const double2*>(ws.p + o);
+                    const double2 qo = *reinterpret_cast<const double2*>(ws.q + o);
+                    pn = make_double2(fma(beta, po.x, c.x), fma(beta, po.y, c.y));
+                    qn = make_double2(fma(beta, qo.x, q0), fma(beta, qo.y, q1));
+                  }
+                  *reinterpret_cast<double2*>(ws.p + o) = pn;
+                  *reinterpret_cast<double2*>(ws.q + o) = qn;
+                  acc = fma(pn.x, qn.x, fma(pn.y, qn.y, acc));
+                });
+  return acc;
+}
+
+// x += (alpha sc) p, r -= alpha q, f = FP32(r), y_1 = f / c on the vectorised path,
+// two points per thread and two pairs in flight per trip; returns the partial r.r.
+__device__ __forceinline__ double pcg_x_vec(const CgDev& a, double alpha, double sc, int blk,
+                                            int nblk) {
+  const CgWork& ws = a.ws;
+  const ChebDev& ch = a.ch;
+  const long long P = a.g.M / 2;  // pairs (M is even on this path)
+  const long long t0 = blk * (long long)blockDim.x + threadIdx.x;
+  const long long nt = (long long)nblk * blockDim.x;
+  const double ax = alpha * sc;
+  double s0 = 0.0, s1 = 0.0;
+  auto one = [&](long long i, double& acc) {
+    const double2 x = reinterpret_cast<const double2*>(ws.x)[i];
+    const double2 p = reinterpret_cast<const double2*>(ws.p)[i];
+    const double2 r = reinterpret_cast<const double2*>(ws.r)[i];
+    const double2 q = reinterpret_cast<const double2*>(ws.q)[i];
+    const double r0 = fma(-alpha, q.x, r.x), r1 = fma(-alpha, q.y, r.y);
+    reinterpret_cast<double2*>(ws.x)[i] = make_double2(fma(ax, p.x, x.x), fma(ax, p.y, x.y));
+    reinterpret_cast<double2*>(ws.r)[i] = make_double2(r0, r1);
+    const float f0 = static_cast<float>(r0), f1 = static_cast<float>(r1);
+    reinterpret_cast<float2*>(ch.res)[i] = make_float2(f0, f1);
+    reinterpret_cast<float2*>(ch.d0)[i] = make_float2(f0 * ch.inv_c, f1 * ch.inv_c);
+    acc = fma(r0, r0, fma(r1, r1, acc));
+  };
+  long long i = t0;
+  for (; i + nt < P; i += 2 * nt) {
+    one(i, s0);
+    one(i + nt, s1);
+  }
+  if (i < P) one(i, s0);
+  return s0 + s1;
+}
+
 // Preconditioned CG (Hestenes-Stiefel with z = p_m(B) r), same start, stopping
 // rule and return value as cg_core.  Per iteration: q = B p and p.q (reduction);
 // x, r and r.r, which also starts the preconditioner res = r, d_0 = res / c,
@@ -495,19 +679,26 @@ __device__ int pcg_core(const CgDev& a, int nblk, int blk) {
   int parity = 0;
   auto part = [&]() { return ws.part + (size_t)parity * 3 * nblk; };
   double s_rr = 0.0, s_bb = 0.0;
-  for_each_point(g, blk, nblk, [&](int x, int y, int z, long long i) {
-    const double bi = a.b[i];
-    const double ri = bi - gop_xyz(g, a.k, var, a.gv, a.x0, x, y, z, i);
-    ws.x[i] = a.x0[i];
-    ws.r[i] = ri;
-    const float rf = static_cast<float>(ri);
-    const float d = rf * ch.inv_c;
-    ch.res[i] = rf;
-    ch.d0[i] = d;
-    ch.y[i] = d;
-    s_rr += ri * ri;
-    s_bb += bi * bi;
-  });
+  if (ch.vec) {
+    if (g.dim == 3)
+      pcg_setup_vec<3>(a, s_rr, s_bb, blk, nblk);
+    else
+      pcg_setup_vec<2>(a, s_rr, s_bb, blk, nblk);
+  } else {
+    for_each_point(g, blk, nblk, [&](int x, int y, int z, long long i) {
+      const double bi = a.b[i];
+      const double ri = bi - gop_xyz(g, a.k, var, a.gv, a.x0, x, y, z, i);
+      ws.x[i] = a.x0[i];
+      ws.r[i] = ri;
+      const float rf = static_cast<float>(ri);
+      const float d = rf * ch.inv_c;
+      ch.res[i] = rf;
+      ch.d0[i] = d;
+      ch.y[i] = d;
+      s_rr += ri * ri;
+      s_bb += bi * bi;
+    });
+  }
   {
     const double v[2] = {s_rr, s_bb};
     block_sum<2>(v, part(), blk);
@@ -561,11 +752,16 @@ __device__ int pcg_core(const CgDev& a, int nblk, int blk) {
         rz = o2[0];
       }
     }
-    // ---- p = z + beta p (p = z on the first iteration)
-    for (long long i = t0; i < M; i += nt) ws.p[i] = it == 0 ? ch.z[i] : fma(beta, ws.p[i], ch.z[i]);
-    bar.sync();
-    // ---- q = B p, p.q
-    {
+    if (ch.vec) {
+      // ---- p = z + beta p and q = B' z + beta q in one pass, p.q
+      const double v[1] = {g.dim == 3 ? pcg_pq_vec<3>(a, ks, beta, it == 0, blk, nblk)
+                                      : pcg_pq_vec<2>(a, ks, beta, it == 0, blk, nblk)};
+      block_sum<1>(v, part(), blk);
+    } else {
+      // ---- p = z + beta p (p = z on the first iteration)
+      for (long long i = t0; i < M; i += nt) ws.p[i] = it == 0 ? ch.z[i] : fma(beta, ws.p[i], ch.z[i]);
+      bar.sync();
+      // ---- q = B p, p.q
       const double v[1] = {cg_matvec_dot(g, ks, var, scaled, a.gv, ws.p, ws.q, blk, nblk)};
       block_sum<1>(v, part(), blk);
     }
@@ -576,16 +772,20 @@ __device__ int pcg_core(const CgDev& a, int nblk, int blk) {
     const double alpha = o2[1];
     // ---- x, r, r.r; start the next preconditioner application
     double s0 = 0.0;
-    for (long long i = t0; i < M; i += nt) {
-      const double ri = fma(-alpha, ws.q[i], ws.r[i]);
-      ws.x[i] = fma(alpha * sc, ws.p[i], ws.x[i]);
-      ws.r[i] = ri;
-      s0 = fma(ri, ri, s0);
-      const float rf = static_cast<float>(ri);
-      const float d = rf * ch.inv_c;
-      ch.res[i] = rf;
-      ch.d0[i] = d;
-      ch.y[i] = d;
+    if (ch.vec) {
+      s0 = pcg_x_vec(a, alpha, sc, blk, nblk);
+    } else {
+      for (long long i = t0; i < M; i += nt) {
+        const double ri = fma(-alpha, ws.q[i], ws.r[i]);
+        ws.x[i] = fma(alpha * sc, ws.p[i], ws.x[i]);
+        ws.r[i] = ri;
+        s0 = fma(ri, ri, s0);
+        const float rf = static_cast<float>(ri);
+        const float d = rf * ch.inv_c;
+        ch.res[i] = rf;
+        ch.d0[i] = d;
+        ch.y[i] = d;
+      }
     }
     {
       const double v[1] = {s0};
@@ -641,14 +841,32 @@ __global__ void __launch_bounds__(CG_THREADS, MINB) cg_kernel(CgDev a) {
     }
   } else {
     unsigned long long dmax = 0ull;
-    for (long long i = t0; i < M; i += nt) {
-      const double xi = x[i];
-      const double wo = a.out[i];
-      const double ln = __dsub_rn(__dadd_rn(xi, a.v[i]), wo);
-      const unsigned long long d = abs_bits(__dsub_rn(ln, a.lam[i]));
-      dmax = d > dmax ? d : dmax;
-      a.lam[i] = ln;
-      a.out[i] = xi;
+    if ((M & 1) == 0) {
+      // two points per thread (every array is 16-byte aligned when M is even)
+      for (long long i = t0; i < M / 2; i += nt) {
+        const double2 xi = reinterpret_cast<const double2*>(x)[i];
+        const double2 wo = reinterpret_cast<const double2*>(a.out)[i];
+        const double2 vi = reinterpret_cast<const double2*>(a.v)[i];
+        const double2 lo = reinterpret_cast<const double2*>(a.lam)[i];
+        const double l0 = __dsub_rn(__dadd_rn(xi.x, vi.x), wo.x);
+        const double l1 = __dsub_rn(__dadd_rn(xi.y, vi.y), wo.y);
+        const unsigned long long d0 = abs_bits(__dsub_rn(l0, lo.x));
+        const unsigned long long d1 = abs_bits(__dsub_rn(l1, lo.y));
+        dmax = d0 > dmax ? d0 : dmax;
+        dmax = d1 > dmax ? d1 : dmax;
+        reinterpret_cast<double2*>(a.lam)[i] = make_double2(l0, l1);
+        reinterpret_cast<double2*>(a.out)[i] = xi;
+      }
+    } else {
+      for (long long i = t0; i < M; i += nt) {
+        const double xi = x[i];
+        const double wo = a.out[i];
+        const double ln = __dsub_rn(__dadd_rn(xi, a.v[i]), wo);
+        const unsigned long long d = abs_bits(__dsub_rn(ln, a.lam[i]));
+        dmax = d > dmax ? d : dmax;
+        a.lam[i] = ln;
+        a.out[i] = xi;
+      }
     }
     dmax = warp_max_u64(dmax);
     if ((threadIdx.x & 31) == 0 && dmax) atomicMax(a.delta, dmax);
