@@ -156,7 +156,7 @@ constexpr int S1Y = TTY + 2;                    // first-step rows
 constexpr int S1PLANE = TPX * S1Y;              // 72 x 18
 constexpr int T2ITEMS = (TPX / 4) * S1Y;        // 324 float4 items of the first step
 
-__global__ void __launch_bounds__(TMA_THREADS, 2) step3d_tma2(const __grid_constant__ CUtensorMap src,
+__global__ void __launch_bounds__(TMA_THREADS, 4) step3d_tma2(const __grid_constant__ CUtensorMap src,
                                                            TmaArgs a) {
   __shared__ __align__(128) float stage[TST][T2STRIDE];
   __shared__ __align__(16) float s1[3][S1PLANE];
@@ -251,14 +251,20 @@ __global__ void __launch_bounds__(TMA_THREADS, 2) step3d_tma2(const __grid_const
       const bool zin = j >= 0 && j < a.nz;
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
-        if (k >= nitem) break;
+        // x-neighbours from the adjacent lanes, which hold the adjacent items of the
+        // same row (a scalar shared load only at row and warp edges: the stride-4
+        // scalar loads conflict in the shared-memory banks)
+        const float4 cur = in_cur[k];
+        const float wsh = __shfl_up_sync(0xffffffffu, cur.w, 1);
+        const float esh = __shfl_down_sync(0xffffffffu, cur.x, 1);
+        if (k >= nitem) continue;
         const int o = (ir[k] + 1) * TPX + 4 * iq[k];
         const float4 nx4 = *reinterpret_cast<const float4*>(Pn + o);
-        const float4 cur = in_cur[k];
         const float4 s4 = *reinterpret_cast<const float4*>(Pc + o - TPX);
         const float4 n4 = *reinterpret_cast<const float4*>(Pc + o + TPX);
-        const float w = iq[k] > 0 ? Pc[o - 1] : 0.f;
-        const float e = iq[k] < TPX / 4 - 1 ? Pc[o + 4] : 0.f;
+        const int lane = tid & 31;
+        const float w = iq[k] == 0 ? 0.f : lane > 0 ? wsh : Pc[o - 1];
+        const float e = iq[k] == TPX / 4 - 1 ? 0.f : lane < 31 ? esh : Pc[o + 4];
         const float4 b4 = in_prev[k];
         float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
         if (zin && ixy[k]) r = step4(c0, rx, ry, rz, cur, w, e, s4, n4, b4, nx4);
@@ -279,12 +285,15 @@ __global__ void __launch_bounds__(TMA_THREADS, 2) step3d_tma2(const __grid_const
     // (d) second step at plane j - 1 from S1 planes j - 2, j - 1 (registers) and j
     const float4 s1_next = *reinterpret_cast<const float4*>(s1[(j + 3) % 3] + c2);
     const int zo = j - 1;
+    const float4 cur = s1_cur;
+    const float wsh = __shfl_up_sync(0xffffffffu, cur.w, 1);   // lanes 0-15 and 16-31: two rows
+    const float esh = __shfl_down_sync(0xffffffffu, cur.x, 1);
     if (zo >= z0 && zo < zend && inside) {
       const float* Q = s1[(j + 2) % 3];   // plane j - 1
-      const float4 cur = s1_cur;
       const float4 s4 = *reinterpret_cast<const float4*>(Q + c2 - TPX);
       const float4 n4 = *reinterpret_cast<const float4*>(Q + c2 + TPX);
-      const float w = Q[c2 - 1], e = Q[c2 + 4];
+      const float w = tx > 0 ? wsh : Q[c2 - 1];
+      const float e = tx < 15 ? esh : Q[c2 + 4];
       const float4 r = step4(c0, rx, ry, rz, cur, w, e, s4, n4, s1_prev, s1_next);
       *reinterpret_cast<float4*>(out + zo * plane + (long long)gy * a.nx + gx) = r;
     }
