@@ -270,9 +270,8 @@ int parareal_adjoint_async(pr_ctx* ctx, const pr_event* log_host, size_t n_event
  *    single-reduction recurrence of Chronopoulos and Gear, whose two inner
  *    products r.r and (B r).r are reduced together: two barriers and one
  *    reduction per iteration for one more vector update per point.  Automatic
- *    picks single-reduction for grids of at most 2^21 points (their vectors
- *    stay in L2 and the barriers dominate an iteration) and textbook above.
- *    The iterates agree to rounding; the iteration counts to about one. */
+ *    is textbook (measured faster from 512^2 points up).  The iterates agree to
+ *    rounding; the iteration counts to about one. */
 /* and one that changes how the fine steps are grouped into launches (the
  * arithmetic of every step is the same):
  *  PR_OPT_F_STEPS_PER_PASS (1 or 2, default 2): the TMA-fed FP32 middle steps

@@ -972,12 +972,13 @@ cudaError_t cg_solve(pr_ctx* c, const CgArgs& in) {
     ch.d1 = ch.d0 + c->g.M;
   }
   const bool big = c->g.M > CG_L2_POINTS;
-  // recurrence: preconditioned, or single-reduction where the barriers dominate
-  // an iteration (vectors resident in L2), textbook otherwise (PR_OPT_G_CG)
-  const int alg = a.ch.m >= 2 ? CG_CHEB
-                  : c->opt_g_cg == 2 ? CG_SINGLE
-                  : c->opt_g_cg == 1 ? CG_TEXTBOOK
-                  : big ? CG_TEXTBOOK : CG_SINGLE;
+  // recurrence: preconditioned, or single-reduction when asked for (PR_OPT_G_CG =
+  // 2), textbook otherwise: measured per iteration at 128^2 .. 1448^2, the
+  // single-reduction recurrence (one barrier and one reduction fewer, one vector
+  // update more) was faster only at 256^2 (12.0 against 13.0 us) and slower from
+  // 512^2 up (15.9 / 15.4, 30.2 / 29.8, 56.9 / 47.9 us): the FP64 pipe and the
+  // extra vector traffic outweigh the barrier it saves
+  const int alg = a.ch.m >= 2 ? CG_CHEB : c->opt_g_cg == 2 ? CG_SINGLE : CG_TEXTBOOK;
   int cap = 0;
   void* fn = nullptr;
   const size_t dsmem = (alg == CG_CHEB && a.ch.tmaps) ? (size_t)CT_SMEM : 0;
