@@ -89,7 +89,10 @@ NOMINAL_FP64_OPS = 625.0  # G FP64-pipe ops/s: 1.25 TFLOP/s nominal / 2 flops pe
 # DRAM bytes (read + write) per cell update of the dominant kernel, from one ncu capture
 # of the current kernel; None where no capture of the current kernel exists.
 # (profiles/step2d_fp64_heat2d_1024x1024.md: 1016.3 MB for 63 x 1048576 updates.)
-NCU_TRAFFIC_PER_LUP = {"heat2d_explicit": 1016.3e6 / (63 * 1048576)}
+NCU_TRAFFIC_PER_LUP = {"heat2d_explicit": 1016.3e6 / (63 * 1048576),
+                       # profiles/step3d_tma2_fp32_heat3d_256cubed_N4.md: 520.4 MB for one
+                       # two-step pass over 4 x 256^3 points (2 updates each)
+                       "heat3d_mixed": 520.4e6 / (2 * 4 * 256 ** 3)}
 
 
 def cost_model_sync(p, st, ms_per_solve):
@@ -959,10 +962,20 @@ def run_ours(args, world, rank, local):
                                       "frac": alg_bytes / (t_fine / 1e3) / 1e9 / hbm_peak}})
     roof["avg_launch_ms"] = t_fine / max(fine_launches, 1)
     lups_per_launch = lups_r / max(fine_launches, 1)
-    roof["algorithmic_bytes_per_launch"] = (alg_bytes / max(fine_launches, 1) if is_mixed
-                                            else 2 * b_elem * lups_per_launch)
     tpl = NCU_TRAFFIC_PER_LUP.get(args.workload)
-    roof["traffic"] = tpl * lups_per_launch if tpl else None
+    if is_mixed:
+        # per launch of the dominant kernel (a middle pass over the active slices):
+        # the algorithmic bytes and the ncu DRAM bytes scaled to the same points
+        steps_per_pass = 2 if (roof.get("passes_per_F", 0) < p["f_steps"]) else 1
+        pts = lups_r / p["f_steps"] / max(sum(s["iterations"] for s in roof_stats), 1)
+        roof["algorithmic_bytes_per_launch"] = 8.0 * pts
+        roof["traffic"] = (tpl * steps_per_pass * pts
+                           if tpl and steps_per_pass == 2 and args.f_per_pass == 2 else None)
+        roof["note"] = ("achieved = algorithmic bytes of all passes of the F phase (first and last "
+                        "with FP64 I/O) / F-phase time; per-launch figures are for a middle pass")
+    else:
+        roof["algorithmic_bytes_per_launch"] = 2 * b_elem * lups_per_launch
+        roof["traffic"] = tpl * lups_per_launch if tpl else None
     # coarse sweep (the predictor and the corrections' CG solves): FP64 pipe
     roof_coarse = None
     if p.get("g_solver") != "thomas" and not args.g_cheb and p.get("kappa") is None:
@@ -979,6 +992,25 @@ def run_ours(args, world, rank, local):
                        if args.g_cheb else "cg_kernel",
                        "cg_iterations": cg_its,
                        "us_per_cg_iteration": t_coarse * 1e3 / max(cg_its, 1)}
+        vec = dim >= 2 and p.get("kappa") is None and p["n"][0] % 4 == 0
+        if args.g_cheb >= 3 and vec:
+            # algorithmic HBM bytes per point: per iteration the m - 1 FP32 Chebyshev
+            # passes (first 12 B: y_1 with its stencil, f, y_2 out; middle 16 B: y_k,
+            # y_k-1, f in, y_k+1 out; last 28 B: also r in and z out in FP64), the fused
+            # direction/operator pass (z with its stencil, p, q in; p, q out: 40 B) and
+            # the solution/residual pass (x, p, r, q in; x, r, f, y_1 out: 56 B); per
+            # solve the start pass (b, x0 in; x, r, f, y_1 out: 40 B) and the fused
+            # correction (x, v, w, lambda in; lambda, w out: 48 B)
+            m = args.g_cheb
+            per_it = 12 + 16 * (m - 3) + 28 + 40 + 56
+            solves = sum(s["coarse_solves"] for s in roof_stats)
+            gbytes = M * (cg_its * per_it + solves * 88)
+            roof_coarse.update({"bound": "hbm", "achieved": gbytes / (t_coarse / 1e3) / 1e9,
+                                "peak": hbm_peak, "unit": "GB/s", "peak_kind": peak_kind,
+                                "bytes_per_point_per_iteration": per_it,
+                                "bytes_per_point_per_solve": 88,
+                                "traffic": None})
+            roof_coarse["frac"] = roof_coarse["achieved"] / hbm_peak
     out = {"metric": "fine GLUP/s", "value": value, "unit": "GLUP/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
