@@ -1021,6 +1021,8 @@ def run_ours(args, world, rank, local):
            "t_fine_ms_per_solve": t_fine / len(roof_stats),
            "t_coarse_ms_per_solve": t_coarse / len(roof_stats),
            "cg_iterations_per_step": sum(s["cg_iterations"] for s in stats) / args.steps,
+           "predictor": {"cg_iterations": roof_stats[-1]["predictor_cg_iterations"],
+                         "t_ms": roof_stats[-1]["t_predictor_ms"]},
            "cost_model": cost_model_sync(p, roof_stats[-1], roof_stats[-1]["t_total_ms"]),
            "roofline": roof, "roofline_coarse": roof_coarse, "fp64_peak": fpk,
            "gpu_launches": launches}

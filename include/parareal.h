@@ -113,6 +113,9 @@ typedef struct pr_stats {
   int verify_rounds;       /* async with verify: fixed-point residual checks made */
   double residual;         /* async with verify: max_i max_x |lam_i - F(lam_{i-1})| at the
                               last check (0 otherwise) */
+  long long predictor_cg_iterations; /* sync: CG iterations of the predictor's N coarse
+                                        solves (included in cg_iterations) */
+  double t_predictor_ms;   /* sync: time of the predictor (included in t_coarse_ms) */
 } pr_stats;
 
 /* Asynchronous run options (Algorithm 2). */

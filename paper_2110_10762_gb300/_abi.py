@@ -36,7 +36,8 @@ class pr_stats(C.Structure):
                 ("coarse_solves", C.c_longlong), ("t_total_ms", C.c_double),
                 ("t_fine_ms", C.c_double), ("t_coarse_ms", C.c_double), ("events", C.c_longlong),
                 ("launches", C.c_longlong), ("fine_cg_iterations", C.c_longlong),
-                ("verify_rounds", C.c_int), ("residual", C.c_double)]
+                ("verify_rounds", C.c_int), ("residual", C.c_double),
+                ("predictor_cg_iterations", C.c_longlong), ("t_predictor_ms", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

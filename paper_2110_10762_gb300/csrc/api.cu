@@ -518,11 +518,13 @@ int parareal_run_sync(pr_ctx* c, double* lam, pr_stats* st) {
   PR_CUDA(c, cudaStreamSynchronize(c->stream));
   nvtxRangePop();
   cudaEventElapsedTime(&t_g, c->ev[0], c->ev[1]);
+  S.t_predictor_ms = t_g;
   for (int i = 1; i <= N; ++i) {
     if (iters[i] < 0) return fail(c, PR_ECUDA, kCoarseWaitExpired);
     S.cg_iterations += iters[i];
     S.coarse_solves += 1;
   }
+  S.predictor_cg_iterations = S.cg_iterations;
 
   int k = 0;
   double maxd = 0.0;

@@ -171,6 +171,7 @@ int run_sync_pipelined(pr_ctx* c, double* lam, pr_stats* st) {
     S.cg_iterations += iters[i];
     S.coarse_solves += 1;
   }
+  S.predictor_cg_iterations = S.cg_iterations;
 
   int k = 0;
   double maxd = 0.0;
