@@ -994,23 +994,21 @@ def run_ours(args, world, rank, local):
                        "us_per_cg_iteration": t_coarse * 1e3 / max(cg_its, 1)}
         vec = dim >= 2 and p.get("kappa") is None and p["n"][0] % 4 == 0
         if args.g_cheb >= 3 and vec:
-            # algorithmic HBM bytes per point: per iteration the m - 1 Chebyshev passes
-            # on BF16-stored vectors (first 6 B: y_1 with its stencil, f, y_2 out;
-            # middle 8 B: y_k, y_k-1, f in, y_k+1 out; last 22 B: also r in and z out in
-            # FP64), the fused direction/operator pass (z with its stencil, p, q in; p,
-            # q out: 40 B) and the solution/residual pass (x, p, r, q in; x, r out in
-            # FP64, f and y_1 in BF16: 52 B); per solve the start pass (b, x0 in; x, r,
-            # f, y_1 out: 36 B) and the fused correction (x, v, w, lambda in; lambda, w
-            # out: 48 B)
+            # algorithmic HBM bytes per point: per iteration the m - 1 FP32 Chebyshev
+            # passes (first 12 B: y_1 with its stencil, f, y_2 out; middle 16 B: y_k,
+            # y_k-1, f in, y_k+1 out; last 28 B: also r in and z out in FP64), the fused
+            # direction/operator pass (z with its stencil, p, q in; p, q out: 40 B) and
+            # the solution/residual pass (x, p, r, q in; x, r, f, y_1 out: 56 B); per
+            # solve the start pass (b, x0 in; x, r, f, y_1 out: 40 B) and the fused
+            # correction (x, v, w, lambda in; lambda, w out: 48 B)
             m = args.g_cheb
-            per_it = 6 + 8 * (m - 3) + 22 + 40 + 52
-            per_solve = 36 + 48
+            per_it = 12 + 16 * (m - 3) + 28 + 40 + 56
             solves = sum(s["coarse_solves"] for s in roof_stats)
-            gbytes = M * (cg_its * per_it + solves * per_solve)
+            gbytes = M * (cg_its * per_it + solves * 88)
             roof_coarse.update({"bound": "hbm", "achieved": gbytes / (t_coarse / 1e3) / 1e9,
                                 "peak": hbm_peak, "unit": "GB/s", "peak_kind": peak_kind,
                                 "bytes_per_point_per_iteration": per_it,
-                                "bytes_per_point_per_solve": per_solve,
+                                "bytes_per_point_per_solve": 88,
                                 "traffic": None})
             roof_coarse["frac"] = roof_coarse["achieved"] / hbm_peak
     out = {"metric": "fine GLUP/s", "value": value, "unit": "GLUP/s", "n_gpus": world,
