@@ -16,7 +16,6 @@
 
 #include <algorithm>
 #include <cooperative_groups.h>
-#include <cuda_bf16.h>
 
 #include "device.cuh"
 #include "tma.cuh"
@@ -46,10 +45,7 @@ struct ChebDev {
   float c0, rx, ry, rz;       // constant-kappa B in FP32 (off-diagonals -r)
   StencilVar<float> gv32;     // variable-kappa B in FP32
   double* z;                  // FP64 preconditioned residual
-  float *res, *y, *d0, *d1;   // FP32 Chebyshev vectors (two-term scalar path)
-  // vectorised path: f and the three-slot ring of iterates stored in BF16 (FP32
-  // arithmetic), in the same allocation
-  __nv_bfloat16 *bres, *by, *bd0, *bd1;
+  float *res, *y, *d0, *d1;   // FP32 Chebyshev vectors
 };
 
 struct CgDev {
@@ -182,32 +178,11 @@ constexpr int CV_ZC = 8;
 
 __device__ __forceinline__ float4 ldf4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 
-// Four consecutive BF16 values (8 bytes) to and from FP32.
-__device__ __forceinline__ float4 ldb4(const __nv_bfloat16* p) {
-  const uint2 u = *reinterpret_cast<const uint2*>(p);
-  __nv_bfloat162 a, b;
-  memcpy(&a, &u.x, 4);
-  memcpy(&b, &u.y, 4);
-  const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
-  return make_float4(fa.x, fa.y, fb.x, fb.y);
-}
-__device__ __forceinline__ void stb4(__nv_bfloat16* p, float4 v) {
-  const __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
-  uint2 u;
-  memcpy(&u.x, &a, 4);
-  memcpy(&u.y, &b, 4);
-  *reinterpret_cast<uint2*>(p) = u;
-}
-__device__ __forceinline__ void stb2(__nv_bfloat16* p, float x, float y) {
-  *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(x, y);
-}
-
 template <int DIM, bool FIRST, bool LAST>
 __device__ __forceinline__ double cheb3_step(const Geom& g, const ChebDev& ch,
-                                             const __nv_bfloat16* __restrict__ yk,
-                                             const __nv_bfloat16* __restrict__ ykm,
-                                             const __nv_bfloat16* __restrict__ f,
-                                             __nv_bfloat16* __restrict__ yn,
+                                             const float* __restrict__ yk,
+                                             const float* __restrict__ ykm,
+                                             const float* __restrict__ f, float* __restrict__ yn,
                                              double* __restrict__ z, const double* __restrict__ r,
                                              float c1, float c2, int blk, int nblk) {
   const unsigned FULL = 0xffffffffu;
@@ -238,29 +213,29 @@ __device__ __forceinline__ double cheb3_step(const Geom& g, const ChebDev& ch,
     const long long row = (DIM == 3 ? (long long)ym * nx : 0) + x;
     float4 prv = zero, cur = zero;
     if (act) {
-      if (s0 > 0) prv = ldb4(yk + (s0 - 1) * sst + row);
-      cur = ldb4(yk + s0 * sst + row);
+      if (s0 > 0) prv = ldf4(yk + (s0 - 1) * sst + row);
+      cur = ldf4(yk + s0 * sst + row);
     }
     for (int sl = s0; sl < s1; ++sl) {
       const long long o = sl * sst + row;
       float4 nxt = zero, mid = zero, fv = zero, pv = zero;
       float wv = 0.f, ev = 0.f;
       if (act) {
-        if (sl + 1 < ns) nxt = ldb4(yk + o + sst);
+        if (sl + 1 < ns) nxt = ldf4(yk + o + sst);
         if (DIM == 3) {
-          if (ym > 0) mid = ldb4(yk + o - nx);
+          if (ym > 0) mid = ldf4(yk + o - nx);
           if (ym + 1 < nm) {
-            const float4 q = ldb4(yk + o + nx);
+            const float4 q = ldf4(yk + o + nx);
             mid.x += q.x;
             mid.y += q.y;
             mid.z += q.z;
             mid.w += q.w;
           }
         }
-        fv = ldb4(f + o);
-        if (!FIRST) pv = ldb4(ykm + o);
-        if (lane == 0 && x > 0) wv = __bfloat162float(yk[o - 1]);
-        if (lane == 31 && x + 4 < nx) ev = __bfloat162float(yk[o + 4]);
+        fv = ldf4(f + o);
+        if (!FIRST) pv = ldf4(ykm + o);
+        if (lane == 0 && x > 0) wv = yk[o - 1];
+        if (lane == 31 && x + 4 < nx) ev = yk[o + 4];
       }
       const float wsh = __shfl_up_sync(FULL, cur.w, 1);
       const float esh = __shfl_down_sync(FULL, cur.x, 1);
@@ -291,7 +266,7 @@ __device__ __forceinline__ double cheb3_step(const Geom& g, const ChebDev& ch,
           acc = fma(r23.x, z23.x, acc);
           acc = fma(r23.y, z23.y, acc);
         } else {
-          stb4(yn + o, out);
+          *reinterpret_cast<float4*>(yn + o) = out;
         }
       }
       prv = cur;
@@ -314,17 +289,14 @@ __device__ __forceinline__ double cheb3_step(const Geom& g, const ChebDev& ch,
 // load is waited before the brick ends.  A wait that expires marks the block
 // dead (it drains its loads, sets ch.err and skips all later TMA work; the
 // solve is reported as failed).
-// BF16 planes: the x halo is 8 elements wide (16 bytes) so that every load
-// starts on a 16-byte boundary.
 constexpr int CT_TX = 64, CT_TY = 16, CT_ZC = 16, CT_ST = 4;
-constexpr int CT_HX = 8;
-constexpr int CT_PX = CT_TX + 2 * CT_HX, CT_PY = CT_TY + 2;
-constexpr unsigned CT_BYTES = CT_PX * CT_PY * sizeof(__nv_bfloat16);
-constexpr int CT_STRIDE = (int)(((CT_BYTES + 127) / 128) * 128 / sizeof(__nv_bfloat16));
-constexpr int CT_SMEM = CT_ST * CT_STRIDE * (int)sizeof(__nv_bfloat16) + CT_ST * 8;
+constexpr int CT_PX = CT_TX + 8, CT_PY = CT_TY + 2;
+constexpr unsigned CT_BYTES = CT_PX * CT_PY * sizeof(float);
+constexpr int CT_STRIDE = (int)(((CT_BYTES + 127) / 128) * 128 / sizeof(float));
+constexpr int CT_SMEM = CT_ST * CT_STRIDE * (int)sizeof(float) + CT_ST * 8;
 
 struct ChebTma {
-  __nv_bfloat16* stage;      // CT_ST stages of CT_STRIDE elements (dynamic shared memory)
+  float* stage;              // CT_ST stages of CT_STRIDE floats (dynamic shared memory)
   unsigned long long* bar;   // CT_ST mbarriers
   unsigned gl;               // loads issued by this block so far (block-uniform)
   bool dead;                 // a bounded wait expired (block-uniform)
@@ -332,10 +304,9 @@ struct ChebTma {
 
 template <bool FIRST, bool LAST>
 __device__ __forceinline__ double cheb_tma_step(const Geom& g, const ChebDev& ch, const void* map,
-                                                const __nv_bfloat16* __restrict__ ykm,
-                                                const __nv_bfloat16* __restrict__ f,
-                                                __nv_bfloat16* __restrict__ yn,
-                                                double* __restrict__ z,
+                                                const float* __restrict__ ykm,
+                                                const float* __restrict__ f,
+                                                float* __restrict__ yn, double* __restrict__ z,
                                                 const double* __restrict__ r, float c1, float c2,
                                                 int blk, int nblk, ChebTma& tm) {
   const int tid = threadIdx.x;
@@ -345,7 +316,7 @@ __device__ __forceinline__ double cheb_tma_step(const Geom& g, const ChebDev& ch
   const long long nbricks = (long long)TXn * TYn * TZn;
   const long long plane = (long long)g.nx * g.ny;
   const float c0 = ch.c0, rx = ch.rx, ry = ch.ry, rz = ch.rz;
-  const int c = (ty + 1) * CT_PX + CT_HX + 4 * tx;  // this thread's first point in a stage
+  const int c = (ty + 1) * CT_PX + 4 + 4 * tx;  // this thread's first point in a stage
   double acc = 0.0;
   for (long long t = blk; t < nbricks && !tm.dead; t += nblk) {
     const int xt = (int)(t % TXn);
@@ -358,9 +329,9 @@ __device__ __forceinline__ double cheb_tma_step(const Geom& g, const ChebDev& ch
     const unsigned gl = tm.gl;
     auto issue = [&](int L) {
       const unsigned q = gl + L;
-      __nv_bfloat16* dst = tm.stage + (q % CT_ST) * CT_STRIDE;
+      float* dst = tm.stage + (q % CT_ST) * CT_STRIDE;
       mbar_arrive_expect_tx(&tm.bar[q % CT_ST], CT_BYTES);
-      tma_load_3d(dst, map, x0 - CT_HX, y0 - 1, z0 - 1 + L, &tm.bar[q % CT_ST]);
+      tma_load_3d(dst, map, x0 - 4, y0 - 1, z0 - 1 + L, &tm.bar[q % CT_ST]);
     };
     if (tid == 0) {
       // the stages were last read through the generic proxy (previous brick or step)
@@ -377,8 +348,8 @@ __device__ __forceinline__ double cheb_tma_step(const Geom& g, const ChebDev& ch
       const long long o = zi * plane + (long long)gy * g.nx + gx;
       float4 fv = make_float4(0.f, 0.f, 0.f, 0.f), pv = fv;
       if (inside) {
-        fv = ldb4(f + o);
-        if (!FIRST) pv = ldb4(ykm + o);
+        fv = ldf4(f + o);
+        if (!FIRST) pv = ldf4(ykm + o);
       }
       while (ok && waited <= L + 1) {
         const unsigned q = gl + waited;
@@ -389,22 +360,16 @@ __device__ __forceinline__ double cheb_tma_step(const Geom& g, const ChebDev& ch
         tm.dead = true;
         break;
       }
-      {
-        const __nv_bfloat16* Pm = tm.stage + ((gl + L - 1) % CT_ST) * CT_STRIDE;
-        const __nv_bfloat16* Pc = tm.stage + ((gl + L) % CT_ST) * CT_STRIDE;
-        const __nv_bfloat16* Pp = tm.stage + ((gl + L + 1) % CT_ST) * CT_STRIDE;
-        const float4 cur = ldb4(Pc + c);
-        // x-neighbours from the adjacent lanes (lanes 0-15 and 16-31 hold two rows);
-        // a shared load only at the row ends
-        const float wsh = __shfl_up_sync(0xffffffffu, cur.w, 1);
-        const float esh = __shfl_down_sync(0xffffffffu, cur.x, 1);
       if (inside) {
-        const float4 s4 = ldb4(Pc + c - CT_PX);
-        const float4 n4 = ldb4(Pc + c + CT_PX);
-        const float4 b4 = ldb4(Pm + c);
-        const float4 f4 = ldb4(Pp + c);
-        const float w = tx > 0 ? wsh : __bfloat162float(Pc[c - 1]);
-        const float e = tx < 15 ? esh : __bfloat162float(Pc[c + 4]);
+        const float* Pm = tm.stage + ((gl + L - 1) % CT_ST) * CT_STRIDE;
+        const float* Pc = tm.stage + ((gl + L) % CT_ST) * CT_STRIDE;
+        const float* Pp = tm.stage + ((gl + L + 1) % CT_ST) * CT_STRIDE;
+        const float4 cur = *reinterpret_cast<const float4*>(Pc + c);
+        const float4 s4 = *reinterpret_cast<const float4*>(Pc + c - CT_PX);
+        const float4 n4 = *reinterpret_cast<const float4*>(Pc + c + CT_PX);
+        const float4 b4 = *reinterpret_cast<const float4*>(Pm + c);
+        const float4 f4 = *reinterpret_cast<const float4*>(Pp + c);
+        const float w = Pc[c - 1], e = Pc[c + 4];
         const float b0 = c0 * cur.x - rx * (w + cur.y) - ry * (s4.x + n4.x) - rz * (b4.x + f4.x);
         const float b1 = c0 * cur.y - rx * (cur.x + cur.z) - ry * (s4.y + n4.y) - rz * (b4.y + f4.y);
         const float b2 = c0 * cur.z - rx * (cur.y + cur.w) - ry * (s4.z + n4.z) - rz * (b4.z + f4.z);
@@ -426,9 +391,8 @@ __device__ __forceinline__ double cheb_tma_step(const Geom& g, const ChebDev& ch
           acc = fma(r23.x, z23.x, acc);
           acc = fma(r23.y, z23.y, acc);
         } else {
-          stb4(yn + o, out);
+          *reinterpret_cast<float4*>(yn + o) = out;
         }
-      }
       }
       // every thread is done with the stage of load L-1: refill it two planes ahead
       __syncthreads();
@@ -463,26 +427,26 @@ __device__ __forceinline__ double cheb3_dispatch(const Geom& g, const ChebDev& c
                                                  int nblk, ChebTma& tm) {
   const int sk = kk % 3;
   const float c1 = ch.c1[kk], c2 = ch.c2[kk];
-  const __nv_bfloat16* yk = sk == 0 ? ch.by : sk == 1 ? ch.bd0 : ch.bd1;
-  const __nv_bfloat16* ykm = sk == 0 ? ch.bd1 : sk == 1 ? ch.by : ch.bd0;
-  __nv_bfloat16* yn = sk == 0 ? ch.bd0 : sk == 1 ? ch.bd1 : ch.by;
+  const float* yk = sk == 0 ? ch.y : sk == 1 ? ch.d0 : ch.d1;
+  const float* ykm = sk == 0 ? ch.d1 : sk == 1 ? ch.y : ch.d0;
+  float* yn = sk == 0 ? ch.d0 : sk == 1 ? ch.d1 : ch.y;
   const bool last = kk == ch.m - 1;
   if (DIM == 3 && ch.tmaps) {
     if (tm.dead) return 0.0;
     const void* map = ch.tmaps + 128 * sk;
     if (kk == 1) {
-      if (last) return cheb_tma_step<true, true>(g, ch, map, ykm, ch.bres, yn, ch.z, r, c1, c2, blk, nblk, tm);
-      return cheb_tma_step<true, false>(g, ch, map, ykm, ch.bres, yn, ch.z, r, c1, c2, blk, nblk, tm);
+      if (last) return cheb_tma_step<true, true>(g, ch, map, ykm, ch.res, yn, ch.z, r, c1, c2, blk, nblk, tm);
+      return cheb_tma_step<true, false>(g, ch, map, ykm, ch.res, yn, ch.z, r, c1, c2, blk, nblk, tm);
     }
-    if (last) return cheb_tma_step<false, true>(g, ch, map, ykm, ch.bres, yn, ch.z, r, c1, c2, blk, nblk, tm);
-    return cheb_tma_step<false, false>(g, ch, map, ykm, ch.bres, yn, ch.z, r, c1, c2, blk, nblk, tm);
+    if (last) return cheb_tma_step<false, true>(g, ch, map, ykm, ch.res, yn, ch.z, r, c1, c2, blk, nblk, tm);
+    return cheb_tma_step<false, false>(g, ch, map, ykm, ch.res, yn, ch.z, r, c1, c2, blk, nblk, tm);
   }
   if (kk == 1) {
-    if (last) return cheb3_step<DIM, true, true>(g, ch, yk, ykm, ch.bres, yn, ch.z, r, c1, c2, blk, nblk);
-    return cheb3_step<DIM, true, false>(g, ch, yk, ykm, ch.bres, yn, ch.z, r, c1, c2, blk, nblk);
+    if (last) return cheb3_step<DIM, true, true>(g, ch, yk, ykm, ch.res, yn, ch.z, r, c1, c2, blk, nblk);
+    return cheb3_step<DIM, true, false>(g, ch, yk, ykm, ch.res, yn, ch.z, r, c1, c2, blk, nblk);
   }
-  if (last) return cheb3_step<DIM, false, true>(g, ch, yk, ykm, ch.bres, yn, ch.z, r, c1, c2, blk, nblk);
-  return cheb3_step<DIM, false, false>(g, ch, yk, ykm, ch.bres, yn, ch.z, r, c1, c2, blk, nblk);
+  if (last) return cheb3_step<DIM, false, true>(g, ch, yk, ykm, ch.res, yn, ch.z, r, c1, c2, blk, nblk);
+  return cheb3_step<DIM, false, false>(g, ch, yk, ykm, ch.res, yn, ch.z, r, c1, c2, blk, nblk);
 }
 
 // ---- vectorised FP64 passes of the preconditioned CG (constant kappa, dim >= 2,
@@ -600,8 +564,8 @@ __device__ __forceinline__ void pcg_setup_vec(const CgDev& a, double& rr, double
                   *reinterpret_cast<double2*>(ws.x + o) = c;
                   *reinterpret_cast<double2*>(ws.r + o) = make_double2(r0, r1);
                   const float f0 = static_cast<float>(r0), f1 = static_cast<float>(r1);
-                  stb2(ch.bres + o, f0, f1);
-                  stb2(ch.bd0 + o, f0 * ch.inv_c, f1 * ch.inv_c);
+                  *reinterpret_cast<float2*>(ch.res + o) = make_float2(f0, f1);
+                  *reinterpret_cast<float2*>(ch.d0 + o) = make_float2(f0 * ch.inv_c, f1 * ch.inv_c);
                   srr = fma(r0, r0, fma(r1, r1, srr));
                   sbb = fma(b.x, b.x, fma(b.y, b.y, sbb));
                 });
@@ -656,8 +620,8 @@ __device__ __forceinline__ double pcg_x_vec(const CgDev& a, double alpha, double
     reinterpret_cast<double2*>(ws.x)[i] = make_double2(fma(ax, p.x, x.x), fma(ax, p.y, x.y));
     reinterpret_cast<double2*>(ws.r)[i] = make_double2(r0, r1);
     const float f0 = static_cast<float>(r0), f1 = static_cast<float>(r1);
-    stb2(ch.bres + 2 * i, f0, f1);
-    stb2(ch.bd0 + 2 * i, f0 * ch.inv_c, f1 * ch.inv_c);
+    reinterpret_cast<float2*>(ch.res)[i] = make_float2(f0, f1);
+    reinterpret_cast<float2*>(ch.d0)[i] = make_float2(f0 * ch.inv_c, f1 * ch.inv_c);
     acc = fma(r0, r0, fma(r1, r1, acc));
   };
   long long i = t0;
@@ -699,8 +663,8 @@ __device__ int pcg_core(const CgDev& a, int nblk, int blk) {
   extern __shared__ __align__(128) unsigned char cheb_smem[];
   ChebTma tm{nullptr, nullptr, 0u, false};
   if (ch.tmaps) {
-    tm.stage = reinterpret_cast<__nv_bfloat16*>(cheb_smem);
-    tm.bar = reinterpret_cast<unsigned long long*>(cheb_smem + CT_ST * CT_STRIDE * sizeof(__nv_bfloat16));
+    tm.stage = reinterpret_cast<float*>(cheb_smem);
+    tm.bar = reinterpret_cast<unsigned long long*>(cheb_smem + CT_ST * CT_STRIDE * sizeof(float));
     if (threadIdx.x == 0) {
       for (int q = 0; q < CT_ST; ++q) mbar_init(&tm.bar[q], 1);
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -1006,14 +970,6 @@ cudaError_t cg_solve(pr_ctx* c, const CgArgs& in) {
     ch.y = ch.res + c->g.M;
     ch.d0 = ch.y + c->g.M;
     ch.d1 = ch.d0 + c->g.M;
-    // BF16 views for the vectorised path, each 16-byte aligned (Mpad = M rounded up
-    // to 8 elements; four of them take at most half of the 4 M floats)
-    __nv_bfloat16* hb = reinterpret_cast<__nv_bfloat16*>(c->cheb_f32);
-    const long long Mpad = (c->g.M + 7) / 8 * 8;
-    ch.bres = hb;
-    ch.by = hb + Mpad;
-    ch.bd0 = hb + 2 * Mpad;
-    ch.bd1 = hb + 3 * Mpad;
   }
   const bool big = c->g.M > CG_L2_POINTS;
   // recurrence: preconditioned, or single-reduction when asked for (PR_OPT_G_CG =
@@ -1138,18 +1094,15 @@ cudaError_t cheb_alloc(pr_ctx* c) {
   if (e == cudaSuccess) e = cudaMalloc(&c->cheb_f32, 4 * g.M * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&c->cheb_err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemsetAsync(c->cheb_err, 0, sizeof(int), c->stream);
-  // 3D constant kappa with nx % 8 == 0 (BF16 rows a multiple of 16 bytes): tensor
-  // maps of the three BF16 ring vectors (after f, at multiples of Mpad elements, as
-  // set up in cg_solve) for the TMA-fed steps; the steps fall back to plain vector
-  // loads when encoding is not possible
-  if (e == cudaSuccess && g.dim == 3 && !c->var_kappa && g.nx % 8 == 0) {
+  // 3D constant kappa with nx % 4 == 0: tensor maps of the three ring vectors
+  // (y, d0, d1 after the FP32 right-hand side f) for the TMA-fed steps; the
+  // steps fall back to plain vector loads when encoding is not possible
+  if (e == cudaSuccess && g.dim == 3 && !c->var_kappa && g.nx % 4 == 0) {
     unsigned char maps[3 * 128];
     bool ok = true;
-    __nv_bfloat16* hb = reinterpret_cast<__nv_bfloat16*>(c->cheb_f32);
-    const long long Mpad = (g.M + 7) / 8 * 8;
     for (int q = 0; q < 3 && ok; ++q)
-      ok = encode_3d_map(maps + 128 * q, hb + (size_t)(q + 1) * Mpad, 2, g.nx, g.ny, g.nz, CT_PX,
-                         CT_PY);
+      ok = encode_f32_3d_map(maps + 128 * q, c->cheb_f32 + (size_t)(q + 1) * g.M, g.nx, g.ny, g.nz,
+                             CT_PX, CT_PY);
     if (ok && cudaMalloc(&c->cheb_tmaps, sizeof maps) == cudaSuccess) {
       e = cudaMemcpyAsync(c->cheb_tmaps, maps, sizeof maps, cudaMemcpyHostToDevice, c->stream);
       if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);

@@ -121,7 +121,7 @@ struct pr_ctx {
   double g_lo = 0, g_hi = 0; // spectrum bounds of I + dT A
   double* cheb_z = nullptr;  // preconditioned residual (M)
   float* cheb_f32 = nullptr; // FP32 Chebyshev vectors (4 M)
-  void* cheb_tmaps = nullptr; // 3D: tensor maps of the three BF16 ring vectors (3 x 128 B, device)
+  void* cheb_tmaps = nullptr; // 3D: tensor maps of the three ring vectors (3 x 128 B, device)
   int* cheb_err = nullptr;   // 3D TMA-fed steps: 1 after a bounded wait expired
   // pipelined driver resources (created lazily)
   cudaStream_t s_sweep = nullptr, s_fine = nullptr;
@@ -193,8 +193,7 @@ cudaError_t fine_apply(pr_ctx* c, const double* in, double* out, int count);
 
 // ---- TMA-fed FP32 3D step (tma_stencil.cu)
 bool tma_prepare(pr_ctx* c);
-bool encode_3d_map(void* out, void* base, int elem_bytes, int nx, int ny, int nz, int box_x,
-                   int box_y);
+bool encode_f32_3d_map(void* out, float* base, int nx, int ny, int nz, int box_x, int box_y);
 cudaError_t tma_step(pr_ctx* c, const float* src, float* dst, int count);
 cudaError_t tma_step2(pr_ctx* c, const float* src, float* dst, int count);
 int fine_launch_count(const pr_ctx* c);

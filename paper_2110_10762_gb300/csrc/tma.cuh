@@ -58,7 +58,7 @@ __device__ __forceinline__ void tma_load_4d(float* dst, const CUtensorMap* map, 
 }
 
 // Tile load of coordinates (x, y, z) of a 3D tensor map into shared memory.
-__device__ __forceinline__ void tma_load_3d(void* dst, const void* map, int x, int y, int z,
+__device__ __forceinline__ void tma_load_3d(float* dst, const void* map, int x, int y, int z,
                                             unsigned long long* bar) {
   asm volatile(
       "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"

@@ -321,22 +321,19 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 }  // namespace
 
-// Tiled tensor map of a 3D array of FP32 (elem_bytes 4) or BF16 (elem_bytes 2)
-// values (x fastest, then y, then z) with a box of box_x x box_y x 1 elements and
-// zero fill outside the array; false when the driver entry point is missing or
-// the encoding is rejected (base not 16-byte aligned, strides not multiples of
-// 16 bytes, ...).  out receives 128 bytes.
-bool encode_3d_map(void* out, void* base, int elem_bytes, int nx, int ny, int nz, int box_x,
-                   int box_y) {
+// Tiled tensor map of a 3D FP32 array (x fastest, then y, then z) with a box of
+// box_x x box_y x 1 elements and zero fill outside the array; false when the
+// driver entry point is missing or the encoding is rejected (base not 16-byte
+// aligned, strides not multiples of 16 bytes, ...).  out receives 128 bytes.
+bool encode_f32_3d_map(void* out, float* base, int nx, int ny, int nz, int box_x, int box_y) {
   PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
-  if (!fn || (elem_bytes != 4 && elem_bytes != 2)) return false;
+  if (!fn) return false;
   const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
-  const cuuint64_t strides[2] = {(cuuint64_t)nx * elem_bytes, (cuuint64_t)nx * ny * elem_bytes};
+  const cuuint64_t strides[2] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4};
   const cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   CUtensorMap m;
-  if (fn(&m, elem_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
-         3, base, dims, strides, box, estr,
+  if (fn(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return false;
