@@ -285,8 +285,7 @@ int parareal_adjoint_async(pr_ctx* ctx, const pr_event* log_host, size_t n_event
 /*  PR_OPT_G_CHEB_STEPS_PER_PASS (1 or 2, default 2): with PR_OPT_G_CHEBYSHEV in 3D
  *    (kappa = 1, n[0] % 4 == 0) the preconditioner's steps after the first run
  *    two per pass over its vectors (temporal blocking, as for the fine steps)
- *    or one.  The same arithmetic per step; the partial sums of r.z are taken in
- *    another order, so results agree to rounding. */
+ *    or one.  The same arithmetic per step: results are bitwise identical. */
 enum pr_option {
   PR_OPT_PIPELINE = 1,
   PR_OPT_PIPELINE_CHUNKS = 2,
