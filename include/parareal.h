@@ -262,7 +262,7 @@ int parareal_adjoint_async(pr_ctx* ctx, const pr_event* log_host, size_t n_event
  *    computed in FP32; the CG recurrences and the test ||r||_2 <= g_rtol
  *    ||b||_2 stay FP64, so the result meets the same residual bound (and,
  *    I + dT A >= I, lies within 2 g_rtol ||b||_2 of the plain CG result).
- *    Needs M doubles and 5 M floats more.  The asynchronous kernel keeps plain
+ *    Needs M doubles and 4 M floats more.  The asynchronous kernel keeps plain
  *    CG. */
 /* and one that changes the coarse CG's recurrence (not its iterates in exact
  * arithmetic, nor its stopping rule):
@@ -282,18 +282,13 @@ int parareal_adjoint_async(pr_ctx* ctx, const pr_event* log_host, size_t n_event
  *    over the state (temporal blocking: one read and one write of the state per
  *    two steps; the first step's values on the halo the second needs are
  *    recomputed per tile) or one.  Results are bitwise identical. */
-/*  PR_OPT_G_CHEB_STEPS_PER_PASS (1 or 2, default 2): with PR_OPT_G_CHEBYSHEV in 3D
- *    (kappa = 1, n[0] % 4 == 0) the preconditioner's steps after the first run
- *    two per pass over its vectors (temporal blocking, as for the fine steps)
- *    or one.  The same arithmetic per step: results are bitwise identical. */
 enum pr_option {
   PR_OPT_PIPELINE = 1,
   PR_OPT_PIPELINE_CHUNKS = 2,
   PR_OPT_CG_BLOCKS_PER_SM = 3,
   PR_OPT_G_CHEBYSHEV = 4,
   PR_OPT_G_CG = 5,
-  PR_OPT_F_STEPS_PER_PASS = 6,
-  PR_OPT_G_CHEB_STEPS_PER_PASS = 7
+  PR_OPT_F_STEPS_PER_PASS = 6
 };
 int parareal_set_option(pr_ctx* ctx, int option, double value);
 

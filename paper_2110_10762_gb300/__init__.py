@@ -8,7 +8,6 @@ from ._abi import (PR_EXPLICIT_EULER, PR_IMPLICIT_EULER, PR_CRANK_NICOLSON, PR_S
                    PR_SOLVER_THOMAS, PR_OK, PR_ENOTCONV, PR_EINVAL, PR_ETIMEOUT, PR_ESTATE,
                    PR_ELOGFULL, PR_ECUDA, PR_ENOMEM, PR_OPT_PIPELINE, PR_OPT_PIPELINE_CHUNKS,
                    PR_OPT_CG_BLOCKS_PER_SM, PR_OPT_G_CHEBYSHEV, PR_OPT_G_CG, PR_OPT_F_STEPS_PER_PASS,
-                   PR_OPT_G_CHEB_STEPS_PER_PASS,
                    pr_problem, pr_stats, pr_async_opts, pr_event)
 from .api import (PararealError, make_async_opts, make_problem, parareal_adjoint,  # noqa: F401
                   parareal_adjoint_async,

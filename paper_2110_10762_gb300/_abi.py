@@ -19,7 +19,6 @@ PR_SOLVER_THOMAS, PR_SOLVER_CG = 0, 1
 PR_OPT_PIPELINE, PR_OPT_PIPELINE_CHUNKS, PR_OPT_CG_BLOCKS_PER_SM, PR_OPT_G_CHEBYSHEV = 1, 2, 3, 4
 PR_OPT_G_CG = 5
 PR_OPT_F_STEPS_PER_PASS = 6
-PR_OPT_G_CHEB_STEPS_PER_PASS = 7
 
 
 class pr_problem(C.Structure):

@@ -457,11 +457,6 @@ int parareal_set_option(pr_ctx* c, int option, double value) {
         return fail(c, PR_EINVAL, "fine steps per pass must be 1 or 2");
       c->opt_f_blocking = (int)value;
       return PR_OK;
-    case PR_OPT_G_CHEB_STEPS_PER_PASS:
-      if (!(value == 1.0 || value == 2.0))
-        return fail(c, PR_EINVAL, "Chebyshev steps per pass must be 1 or 2");
-      c->opt_g_cheb_pair = (int)value;
-      return PR_OK;
     case PR_OPT_G_CG:
       if (!(value == 0.0 || value == 1.0 || value == 2.0))
         return fail(c, PR_EINVAL, "coarse CG recurrence must be 0, 1 or 2");

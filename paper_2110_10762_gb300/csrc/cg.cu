@@ -37,11 +37,8 @@ constexpr int CHEB_MAX = 64;
 struct ChebDev {
   int m;                      // 0: plain CG
   int vec;                    // 1: vectorised three-term steps (dim >= 2, kappa = 1, nx % 4 == 0)
-  const unsigned char* tmaps; // 3D: tensor maps of the ring slots y, d0, d1, e (128 B each,
-                              // device): four with 72 x 18 boxes, then four with 72 x 20
+  const unsigned char* tmaps; // 3D: tensor maps of y, d0, d1 (128 B each, device), or NULL
   int* err;                   // set to 1 when a bounded wait of the TMA-fed steps expired
-  int pair;                   // 3D TMA path: two Chebyshev steps per pass after the first
-  float* e;                   // fourth ring slot of the TMA path
   double lo, hi;              // spectrum bounds of B
   float inv_c;                // 1 / centre of [lo, hi]
   float c1[CHEB_MAX], c2[CHEB_MAX];  // step k: d_k = c1[k] d_{k-1} + c2[k] res_k
@@ -163,28 +160,6 @@ __device__ __forceinline__ double cheb_step(const Geom& g, const ChebDev& ch, bo
     }
   }
   return acc;
-}
-
-// One three-term Chebyshev update at four points, with explicit FMAs in a fixed
-// order (so that the one-step and two-step passes round identically):
-//   B u = c0 u - rx (w + e) - ry sn - rz bf,   u' = u + c1 (u - u_prev) + c2 (f - B u),
-// where sn / bf are the sums of the two neighbours along the other axes.
-__device__ __forceinline__ float cheb_pt(float c0, float rx, float ry, float rz, float c1, float c2,
-                                         float u, float w, float e, float sn, float bf, float up,
-                                         float f) {
-  const float bu = fmaf(-rz, bf, fmaf(-ry, sn, fmaf(-rx, w + e, c0 * u)));
-  return fmaf(c2, f - bu, fmaf(c1, u - up, u));
-}
-
-__device__ __forceinline__ float4 cheb_pt4(float c0, float rx, float ry, float rz, float c1, float c2,
-                                           float4 u, float w, float e, float4 s4, float4 n4,
-                                           float4 b4, float4 f4, float4 up, float4 f) {
-  float4 o;
-  o.x = cheb_pt(c0, rx, ry, rz, c1, c2, u.x, w, u.y, s4.x + n4.x, b4.x + f4.x, up.x, f.x);
-  o.y = cheb_pt(c0, rx, ry, rz, c1, c2, u.y, u.x, u.z, s4.y + n4.y, b4.y + f4.y, up.y, f.y);
-  o.z = cheb_pt(c0, rx, ry, rz, c1, c2, u.z, u.y, u.w, s4.z + n4.z, b4.z + f4.z, up.z, f.z);
-  o.w = cheb_pt(c0, rx, ry, rz, c1, c2, u.w, u.z, e, s4.w + n4.w, b4.w + f4.w, up.w, f.w);
-  return o;
 }
 
 // Vectorised Chebyshev step in three-term form (constant kappa, dim >= 2,
@@ -318,24 +293,10 @@ constexpr int CT_TX = 64, CT_TY = 16, CT_ZC = 16, CT_ST = 4;
 constexpr int CT_PX = CT_TX + 8, CT_PY = CT_TY + 2;
 constexpr unsigned CT_BYTES = CT_PX * CT_PY * sizeof(float);
 constexpr int CT_STRIDE = (int)(((CT_BYTES + 127) / 128) * 128 / sizeof(float));
-constexpr int CT_SMEM1 = CT_ST * CT_STRIDE * (int)sizeof(float) + CT_ST * 8;
-// two steps per pass: bricks of 64 x 12 columns, input planes with a 2-point halo
-// (72 x 16) and a three-plane ring of first-step values on the 72 x 14 region the
-// second step needs: 252 float4 items, one per thread
-constexpr int C2_TY = 12;
-constexpr int C2_PY = C2_TY + 4;
-constexpr int C2_S1Y = C2_TY + 2;
-constexpr unsigned C2_BYTES = CT_PX * C2_PY * sizeof(float);
-constexpr int C2_STRIDE = (int)(((C2_BYTES + 127) / 128) * 128 / sizeof(float));
-constexpr int C2_S1 = CT_PX * C2_S1Y;                // floats per first-step plane
-constexpr int C2_ITEMS = (CT_PX / 4) * C2_S1Y;       // 252 float4 items
-constexpr int CT_SMEM2 = CT_ST * C2_STRIDE * (int)sizeof(float) + 3 * C2_S1 * (int)sizeof(float) +
-                         CT_ST * 8;
-constexpr int CT_SMEM = CT_SMEM2 > CT_SMEM1 ? CT_SMEM2 : CT_SMEM1;
+constexpr int CT_SMEM = CT_ST * CT_STRIDE * (int)sizeof(float) + CT_ST * 8;
 
 struct ChebTma {
-  float* stage;              // CT_ST stages (CT_STRIDE or, two steps per pass, C2_STRIDE floats)
-  float* s1;                 // two steps per pass: three first-step planes of C2_S1 floats
+  float* stage;              // CT_ST stages of CT_STRIDE floats (dynamic shared memory)
   unsigned long long* bar;   // CT_ST mbarriers
   unsigned gl;               // loads issued by this block so far (block-uniform)
   bool dead;                 // a bounded wait expired (block-uniform)
@@ -409,7 +370,15 @@ __device__ __forceinline__ double cheb_tma_step(const Geom& g, const ChebDev& ch
         const float4 b4 = *reinterpret_cast<const float4*>(Pm + c);
         const float4 f4 = *reinterpret_cast<const float4*>(Pp + c);
         const float w = Pc[c - 1], e = Pc[c + 4];
-        const float4 out = cheb_pt4(c0, rx, ry, rz, c1, c2, cur, w, e, s4, n4, b4, f4, pv, fv);
+        const float b0 = c0 * cur.x - rx * (w + cur.y) - ry * (s4.x + n4.x) - rz * (b4.x + f4.x);
+        const float b1 = c0 * cur.y - rx * (cur.x + cur.z) - ry * (s4.y + n4.y) - rz * (b4.y + f4.y);
+        const float b2 = c0 * cur.z - rx * (cur.y + cur.w) - ry * (s4.z + n4.z) - rz * (b4.z + f4.z);
+        const float b3 = c0 * cur.w - rx * (cur.z + e) - ry * (s4.w + n4.w) - rz * (b4.w + f4.w);
+        float4 out;
+        out.x = cur.x + c1 * (cur.x - pv.x) + c2 * (fv.x - b0);
+        out.y = cur.y + c1 * (cur.y - pv.y) + c2 * (fv.y - b1);
+        out.z = cur.z + c1 * (cur.z - pv.z) + c2 * (fv.z - b2);
+        out.w = cur.w + c1 * (cur.w - pv.w) + c2 * (fv.w - b3);
         if (LAST) {
           const double2 z01 = make_double2(out.x, out.y), z23 = make_double2(out.z, out.w);
           double2* zp = reinterpret_cast<double2*>(z + o);
@@ -450,227 +419,21 @@ __device__ __forceinline__ double cheb_tma_step(const Geom& g, const ChebDev& ch
   return acc;
 }
 
-// Two Chebyshev steps per pass (3D TMA path; temporal blocking of the
-// preconditioner): from y_k, y_{k-1} and f it computes y_{k+1} on the 72 x 18
-// region around each 64 x 16 brick column (the same update as cheb_tma_step,
-// with y_{k-1} and f by float4 loads and every value outside the grid set to
-// the Dirichlet zero) into a three-plane shared ring, stores its brick-interior
-// part (the next pass reads it as y_{k-1}), and from the ring computes y_{k+2}
-// (or, LAST, z = y_{k+2} in FP64 and the partial r.z).  y_k planes come by TMA
-// with a 2-point halo (72 x 20); each thread carries the z-neighbours of its
-// first-step items and of its second-step column in registers, and its y_k value
-// for the second step; x-neighbours by warp shuffles.  One block barrier per
-// plane; the ring rotations are those of step3d_tma2 in tma_stencil.cu.
-template <bool LAST>
-__device__ __forceinline__ double cheb_tma_step2(const Geom& g, const ChebDev& ch, const void* map,
-                                                 const float* __restrict__ ykm,
-                                                 const float* __restrict__ f,
-                                                 float* __restrict__ yn1, float* __restrict__ yn2,
-                                                 double* __restrict__ z,
-                                                 const double* __restrict__ r, float c1a,
-                                                 float c2a, float c1b, float c2b, int blk,
-                                                 int nblk, ChebTma& tm) {
-  const unsigned FULL = 0xffffffffu;
-  const int tid = threadIdx.x;
-  const int tx = tid & 15, ty = tid >> 4, lane = tid & 31;
-  const int TXn = (g.nx + CT_TX - 1) / CT_TX, TYn = (g.ny + C2_TY - 1) / C2_TY;
-  const int TZn = (g.nz + CT_ZC - 1) / CT_ZC;
-  const long long nbricks = (long long)TXn * TYn * TZn;
-  const long long plane = (long long)g.nx * g.ny;
-  const float c0 = ch.c0, rx = ch.rx, ry = ch.ry, rz = ch.rz;
-  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-  // first-step item of this thread: row ir (grid y = y0 - 1 + ir), float4 column iq
-  // (grid x = x0 - 4 + 4 iq); stage row ir + 1, column 4 iq
-  const bool item = tid < C2_ITEMS;
-  const int ir = tid / (CT_PX / 4), iq = tid % (CT_PX / 4);
-  const int oi = (ir + 1) * CT_PX + 4 * iq;
-  const bool two = ty < C2_TY;                    // threads with a second-step point
-  const int cs = (ty + 2) * CT_PX + 4 + 4 * tx;   // second-step point in a 72 x 16 stage
-  const int c2 = (ty + 1) * CT_PX + 4 + 4 * tx;   // and in a first-step plane
-  double acc = 0.0;
-  for (long long t = blk; t < nbricks && !tm.dead; t += nblk) {
-    const int xt = (int)(t % TXn);
-    const long long u = t / TXn;
-    const int yt = (int)(u % TYn);
-    const int zt = (int)(u / TYn);
-    const int x0 = xt * CT_TX, y0 = yt * C2_TY, z0 = zt * CT_ZC;
-    const int z1 = min(z0 + CT_ZC, g.nz);
-    const int nload = z1 - z0 + 4;   // planes z0-2 .. z1+1; load L = plane - (z0 - 2)
-    const unsigned gl = tm.gl;
-    auto issue = [&](int L) {
-      const unsigned q = gl + L;
-      float* dst = tm.stage + (q % CT_ST) * C2_STRIDE;
-      mbar_arrive_expect_tx(&tm.bar[q % CT_ST], C2_BYTES);
-      tma_load_3d(dst, map, x0 - 4, y0 - 2, z0 - 2 + L, &tm.bar[q % CT_ST]);
-    };
-    if (tid == 0) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      for (int L = 0; L < CT_ST && L < nload; ++L) issue(L);
-    }
-    int issued = CT_ST < nload ? CT_ST : nload;
-    int waited = 0;
-    bool ok = true;
-    auto wait_upto = [&](int L) {
-      while (ok && waited <= L) {
-        const unsigned q = gl + waited;
-        ok = mbar_wait(&tm.bar[q % CT_ST], (q / CT_ST) & 1u);
-        if (ok) ++waited;
-      }
-    };
-    auto stage_of = [&](int L) { return tm.stage + ((gl + L) % CT_ST) * C2_STRIDE; };
-    const int gx1 = x0 - 4 + 4 * iq, gy1 = y0 - 1 + ir;
-    const bool ixy = item && gx1 >= 0 && gx1 < g.nx && gy1 >= 0 && gy1 < g.ny;
-    const long long og = ixy ? (long long)gy1 * g.nx + gx1 : 0;
-    // interior items: their first-step values are the next pass's y_{k-1}
-    const bool interior = ixy && ir >= 1 && ir <= C2_TY && iq >= 1 && iq <= CT_TX / 4;
-    const int gx = x0 + 4 * tx, gy = y0 + ty;
-    const bool inside = two && gx < g.nx && gy < g.ny;
-    const long long og2 = inside ? (long long)gy * g.nx + gx : 0;
-    float4 in_prev = zero, in_cur = zero, s1_prev = zero, s1_cur = zero, yk_keep = zero;
-    // prologue: own input columns of planes z0-2 and z0-1
-    wait_upto(1);
-    if (__syncthreads_or(!ok)) {
-      tm.dead = true;
-    } else if (item) {
-      in_prev = *reinterpret_cast<const float4*>(stage_of(0) + oi);
-      in_cur = *reinterpret_cast<const float4*>(stage_of(1) + oi);
-    }
-    __syncthreads();
-    if (!tm.dead && CT_ST < nload) {
-      if (tid == 0) {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        issue(CT_ST);
-      }
-      ++issued;
-    }
-    for (int j = z0 - 1; j <= z1 && !tm.dead; ++j) {
-      const int Lj = j - z0 + 2;
-      const bool zin = j >= 0 && j < g.nz;
-      const bool zout = j - 1 >= z0 && j - 1 < z1;   // second step of plane j-1 is this brick's
-      wait_upto(Lj + 1);
-      if (__syncthreads_or(!ok)) {
-        tm.dead = true;
-        break;
-      }
-      // (b) first step at plane j
-      const float* Pc = stage_of(Lj);
-      float* S = tm.s1 + ((j + 3) % 3) * C2_S1;
-      {
-        const float4 cur = in_cur;
-        const float wsh = __shfl_up_sync(FULL, cur.w, 1);
-        const float esh = __shfl_down_sync(FULL, cur.x, 1);
-        if (item) {
-          const float4 nx4 = *reinterpret_cast<const float4*>(stage_of(Lj + 1) + oi);
-          float4 y1 = zero;
-          if (zin && ixy) {
-            const float4 s4 = *reinterpret_cast<const float4*>(Pc + oi - CT_PX);
-            const float4 n4 = *reinterpret_cast<const float4*>(Pc + oi + CT_PX);
-            const float w = iq == 0 ? 0.f : lane > 0 ? wsh : Pc[oi - 1];
-            const float e = iq == CT_PX / 4 - 1 ? 0.f : lane < 31 ? esh : Pc[oi + 4];
-            const float4 fv = ldf4(f + j * plane + og);     // f and y_{k-1} at the item
-            const float4 pv = ldf4(ykm + j * plane + og);
-            y1 = cheb_pt4(c0, rx, ry, rz, c1a, c2a, cur, w, e, s4, n4, in_prev, nx4, pv, fv);
-            if (interior && j >= z0 && j < z1)
-              *reinterpret_cast<float4*>(yn1 + j * plane + og) = y1;
-          }
-          *reinterpret_cast<float4*>(S + ir * CT_PX + 4 * iq) = y1;
-          in_prev = cur;
-          in_cur = nx4;
-        }
-      }
-      const float4 yk_new = two ? *reinterpret_cast<const float4*>(Pc + cs) : zero;   // y_k, plane j
-      // (c) first-step plane j complete; the input stage of plane j has had its last use
-      __syncthreads();
-      if (Lj + CT_ST < nload) {
-        if (tid == 0) {
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          issue(Lj + CT_ST);
-        }
-        ++issued;
-      }
-      // (d) second step at plane j - 1 (threads with ty < 12; lanes 0-15 and 16-31 hold
-      // two rows)
-      const float4 s1_next = two ? *reinterpret_cast<const float4*>(S + c2) : zero;
-      const float4 cur = s1_cur;
-      const float wsh = __shfl_up_sync(FULL, cur.w, 1);
-      const float esh = __shfl_down_sync(FULL, cur.x, 1);
-      if (zout && inside) {
-        const float4 f_own = ldf4(f + (j - 1) * plane + og2);
-        const float* Q = tm.s1 + ((j + 2) % 3) * C2_S1;   // plane j - 1
-        const float4 s4 = *reinterpret_cast<const float4*>(Q + c2 - CT_PX);
-        const float4 n4 = *reinterpret_cast<const float4*>(Q + c2 + CT_PX);
-        const float w = tx > 0 ? wsh : Q[c2 - 1];
-        const float e = tx < 15 ? esh : Q[c2 + 4];
-        const float4 y2 =
-            cheb_pt4(c0, rx, ry, rz, c1b, c2b, cur, w, e, s4, n4, s1_prev, s1_next, yk_keep, f_own);
-        const long long o = (j - 1) * plane + og2;
-        if (LAST) {
-          const double2 z01 = make_double2(y2.x, y2.y), z23 = make_double2(y2.z, y2.w);
-          double2* zp = reinterpret_cast<double2*>(z + o);
-          zp[0] = z01;
-          zp[1] = z23;
-          const double2* rp = reinterpret_cast<const double2*>(r + o);
-          const double2 r01 = rp[0], r23 = rp[1];
-          acc = fma(r01.x, z01.x, acc);
-          acc = fma(r01.y, z01.y, acc);
-          acc = fma(r23.x, z23.x, acc);
-          acc = fma(r23.y, z23.y, acc);
-        } else {
-          *reinterpret_cast<float4*>(yn2 + o) = y2;
-        }
-      }
-      s1_prev = s1_cur;
-      s1_cur = s1_next;
-      yk_keep = yk_new;
-    }
-    if (tm.dead) {
-      if (tid == 0) {
-        atomicExch(ch.err, 1);
-        for (int L = waited; L < issued; ++L) {
-          const unsigned q = gl + L;
-          mbar_wait(&tm.bar[q % CT_ST], (q / CT_ST) & 1u);
-        }
-      }
-      __syncthreads();
-    }
-    tm.gl = gl + nload;
-  }
-  return acc;
-}
-
 // Steps k = 1..m-1 of the vectorised preconditioner: y_1 = f / c is in ring
 // slot 1 (written with f by the pass that updated r), y_k in slot k % 3.
-__device__ __forceinline__ float* ring4(const ChebDev& ch, int s) {
-  return s == 0 ? ch.y : s == 1 ? ch.d0 : s == 2 ? ch.d1 : ch.e;
-}
-
-// Step kk (and, with pair, step kk + 1) of the vectorised preconditioner.  The
-// 3D TMA path keeps y_k in ring slot k % 4 (four slots: a two-step pass reads
-// y_k and y_{k-1} while it writes y_{k+1} and y_{k+2}); the other vectorised
-// paths in slot k % 3.  Either way y_1 = f / c is in slot 1, written with f by
-// the pass that updated r.
 template <int DIM>
 __device__ __forceinline__ double cheb3_dispatch(const Geom& g, const ChebDev& ch,
-                                                 const double* __restrict__ r, int kk, bool pair,
-                                                 int blk, int nblk, ChebTma& tm) {
+                                                 const double* __restrict__ r, int kk, int blk,
+                                                 int nblk, ChebTma& tm) {
+  const int sk = kk % 3;
+  const float c1 = ch.c1[kk], c2 = ch.c2[kk];
+  const float* yk = sk == 0 ? ch.y : sk == 1 ? ch.d0 : ch.d1;
+  const float* ykm = sk == 0 ? ch.d1 : sk == 1 ? ch.y : ch.d0;
+  float* yn = sk == 0 ? ch.d0 : sk == 1 ? ch.d1 : ch.y;
+  const bool last = kk == ch.m - 1;
   if (DIM == 3 && ch.tmaps) {
     if (tm.dead) return 0.0;
-    const int sk = kk % 4;
-    const float* ykm = ring4(ch, (kk + 3) % 4);
-    float* yn = ring4(ch, (kk + 1) % 4);
-    if (pair) {
-      const void* map = ch.tmaps + 128 * (4 + sk);
-      float* yn2 = ring4(ch, (kk + 2) % 4);
-      const float c1a = ch.c1[kk], c2a = ch.c2[kk], c1b = ch.c1[kk + 1], c2b = ch.c2[kk + 1];
-      if (kk + 1 == ch.m - 1)
-        return cheb_tma_step2<true>(g, ch, map, ykm, ch.res, yn, yn2, ch.z, r, c1a, c2a, c1b, c2b,
-                                    blk, nblk, tm);
-      return cheb_tma_step2<false>(g, ch, map, ykm, ch.res, yn, yn2, ch.z, r, c1a, c2a, c1b, c2b,
-                                   blk, nblk, tm);
-    }
     const void* map = ch.tmaps + 128 * sk;
-    const float c1 = ch.c1[kk], c2 = ch.c2[kk];
-    const bool last = kk == ch.m - 1;
     if (kk == 1) {
       if (last) return cheb_tma_step<true, true>(g, ch, map, ykm, ch.res, yn, ch.z, r, c1, c2, blk, nblk, tm);
       return cheb_tma_step<true, false>(g, ch, map, ykm, ch.res, yn, ch.z, r, c1, c2, blk, nblk, tm);
@@ -678,12 +441,6 @@ __device__ __forceinline__ double cheb3_dispatch(const Geom& g, const ChebDev& c
     if (last) return cheb_tma_step<false, true>(g, ch, map, ykm, ch.res, yn, ch.z, r, c1, c2, blk, nblk, tm);
     return cheb_tma_step<false, false>(g, ch, map, ykm, ch.res, yn, ch.z, r, c1, c2, blk, nblk, tm);
   }
-  const int sk = kk % 3;
-  const float c1 = ch.c1[kk], c2 = ch.c2[kk];
-  const float* yk = sk == 0 ? ch.y : sk == 1 ? ch.d0 : ch.d1;
-  const float* ykm = sk == 0 ? ch.d1 : sk == 1 ? ch.y : ch.d0;
-  float* yn = sk == 0 ? ch.d0 : sk == 1 ? ch.d1 : ch.y;
-  const bool last = kk == ch.m - 1;
   if (kk == 1) {
     if (last) return cheb3_step<DIM, true, true>(g, ch, yk, ykm, ch.res, yn, ch.z, r, c1, c2, blk, nblk);
     return cheb3_step<DIM, true, false>(g, ch, yk, ykm, ch.res, yn, ch.z, r, c1, c2, blk, nblk);
@@ -904,18 +661,16 @@ __device__ int pcg_core(const CgDev& a, int nblk, int blk) {
   const PcgBarrier bar{ch.tmaps != nullptr};
   // TMA-fed 3D steps: stage ring and mbarriers in dynamic shared memory
   extern __shared__ __align__(128) unsigned char cheb_smem[];
-  ChebTma tm{nullptr, nullptr, nullptr, 0u, false};
+  ChebTma tm{nullptr, nullptr, 0u, false};
   if (ch.tmaps) {
-    // stages at the larger (two-step) pitch, then the first-step ring, then the barriers
     tm.stage = reinterpret_cast<float*>(cheb_smem);
-    tm.s1 = tm.stage + CT_ST * C2_STRIDE;
-    tm.bar = reinterpret_cast<unsigned long long*>(tm.s1 + 3 * C2_S1);
+    tm.bar = reinterpret_cast<unsigned long long*>(cheb_smem + CT_ST * CT_STRIDE * sizeof(float));
     if (threadIdx.x == 0) {
       for (int q = 0; q < CT_ST; ++q) mbar_init(&tm.bar[q], 1);
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       // the tensor maps were written to global memory before the launch
-      for (int q = 0; q < 8; ++q)
+      for (int q = 0; q < 3; ++q)
         asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(ch.tmaps + 128 * q)
                      : "memory");
     }
@@ -971,18 +726,15 @@ __device__ int pcg_core(const CgDev& a, int nblk, int blk) {
   double rz = 0.0, beta = 0.0;
   while (true) {
     // ---- z = p_m(B) r: steps k = 1..m-1 (res, d_0, y set by the previous pass)
-    for (int kk = 1; kk < ch.m;) {
+    for (int kk = 1; kk < ch.m; ++kk) {
       const float c1 = ch.c1[kk], c2 = ch.c2[kk];
       const float* dp = (kk & 1) ? ch.d0 : ch.d1;
       float* dn = (kk & 1) ? ch.d1 : ch.d0;
-      // two steps per pass on the 3D TMA path after the first step
-      const bool pair = ch.vec && ch.tmaps && ch.pair && kk >= 2 && kk + 1 <= ch.m - 1;
-      const int klast = pair ? kk + 1 : kk;
-      const bool last = klast == ch.m - 1;
+      const bool last = kk == ch.m - 1;
       double s_rz = 0.0;
       if (ch.vec)
-        s_rz = g.dim == 3 ? cheb3_dispatch<3>(g, ch, ws.r, kk, pair, blk, nblk, tm)
-                          : cheb3_dispatch<2>(g, ch, ws.r, kk, pair, blk, nblk, tm);
+        s_rz = g.dim == 3 ? cheb3_dispatch<3>(g, ch, ws.r, kk, blk, nblk, tm)
+                          : cheb3_dispatch<2>(g, ch, ws.r, kk, blk, nblk, tm);
       else if (last)
         s_rz = cheb_step<true>(g, ch, var, dp, dn, ch.res, ch.y, ch.z, ws.r, c1, c2, blk, nblk);
       else
@@ -999,7 +751,6 @@ __device__ int pcg_core(const CgDev& a, int nblk, int blk) {
         beta = o2[1];
         rz = o2[0];
       }
-      kk = klast + 1;
     }
     if (ch.vec) {
       // ---- p = z + beta p and q = B' z + beta q in one pass, p.q
@@ -1196,7 +947,6 @@ cudaError_t cg_solve(pr_ctx* c, const CgArgs& in) {
     ch.vec = (c->g.dim >= 2 && !c->var_kappa && c->g.nx % 4 == 0) ? 1 : 0;
     ch.tmaps = (ch.vec && c->g.dim == 3) ? static_cast<const unsigned char*>(c->cheb_tmaps) : nullptr;
     ch.err = c->cheb_err;
-    ch.pair = c->opt_g_cheb_pair == 2 ? 1 : 0;
     ch.lo = c->g_lo;
     ch.hi = c->g_hi;
     // Chebyshev recurrence coefficients on [lo, hi] (centre cc, half width ee)
@@ -1220,7 +970,6 @@ cudaError_t cg_solve(pr_ctx* c, const CgArgs& in) {
     ch.y = ch.res + c->g.M;
     ch.d0 = ch.y + c->g.M;
     ch.d1 = ch.d0 + c->g.M;
-    ch.e = ch.d1 + c->g.M;
   }
   const bool big = c->g.M > CG_L2_POINTS;
   // recurrence: preconditioned, or single-reduction when asked for (PR_OPT_G_CG =
@@ -1342,19 +1091,18 @@ cudaError_t cheb_alloc(pr_ctx* c) {
   if (c->cheb_z) return cudaSuccess;
   const Geom& g = c->g;
   cudaError_t e = cudaMalloc(&c->cheb_z, g.M * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&c->cheb_f32, 5 * g.M * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&c->cheb_f32, 4 * g.M * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&c->cheb_err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemsetAsync(c->cheb_err, 0, sizeof(int), c->stream);
-  // 3D constant kappa with nx % 4 == 0: tensor maps of the four ring vectors
-  // (y, d0, d1, e after the FP32 right-hand side f) for the TMA-fed steps, with
-  // 72 x 18 boxes (one step per pass) and 72 x 20 boxes (two); the steps fall
-  // back to plain vector loads when encoding is not possible
+  // 3D constant kappa with nx % 4 == 0: tensor maps of the three ring vectors
+  // (y, d0, d1 after the FP32 right-hand side f) for the TMA-fed steps; the
+  // steps fall back to plain vector loads when encoding is not possible
   if (e == cudaSuccess && g.dim == 3 && !c->var_kappa && g.nx % 4 == 0) {
-    unsigned char maps[8 * 128];
+    unsigned char maps[3 * 128];
     bool ok = true;
-    for (int q = 0; q < 8 && ok; ++q)
-      ok = encode_f32_3d_map(maps + 128 * q, c->cheb_f32 + (size_t)(q % 4 + 1) * g.M, g.nx, g.ny,
-                             g.nz, CT_PX, q < 4 ? CT_PY : C2_PY);
+    for (int q = 0; q < 3 && ok; ++q)
+      ok = encode_f32_3d_map(maps + 128 * q, c->cheb_f32 + (size_t)(q + 1) * g.M, g.nx, g.ny, g.nz,
+                             CT_PX, CT_PY);
     if (ok && cudaMalloc(&c->cheb_tmaps, sizeof maps) == cudaSuccess) {
       e = cudaMemcpyAsync(c->cheb_tmaps, maps, sizeof maps, cudaMemcpyHostToDevice, c->stream);
       if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);

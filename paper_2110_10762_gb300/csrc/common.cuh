@@ -118,11 +118,10 @@ struct pr_ctx {
   int opt_cg_bps = 0;        // CG blocks per SM (0 = automatic)
   int opt_g_cheb = 0;        // Chebyshev steps of the coarse CG preconditioner (0 = plain CG)
   int opt_g_cg = 0;          // coarse CG recurrence: 0 automatic, 1 textbook, 2 single-reduction
-  int opt_g_cheb_pair = 2;   // Chebyshev steps per pass on the 3D TMA path (1 or 2)
   double g_lo = 0, g_hi = 0; // spectrum bounds of I + dT A
   double* cheb_z = nullptr;  // preconditioned residual (M)
-  float* cheb_f32 = nullptr; // FP32 Chebyshev vectors (5 M: f and a ring of four iterates)
-  void* cheb_tmaps = nullptr; // 3D: tensor maps of the four ring vectors, two box heights (8 x 128 B)
+  float* cheb_f32 = nullptr; // FP32 Chebyshev vectors (4 M)
+  void* cheb_tmaps = nullptr; // 3D: tensor maps of the three ring vectors (3 x 128 B, device)
   int* cheb_err = nullptr;   // 3D TMA-fed steps: 1 after a bounded wait expired
   // pipelined driver resources (created lazily)
   cudaStream_t s_sweep = nullptr, s_fine = nullptr;

@@ -77,34 +77,6 @@ def test_pcg_vectorised_steps(n, m):
     assert np.linalg.norm(r) <= 1e-12 * np.linalg.norm(b)
 
 
-@pytest.mark.parametrize("n", [(136, 30, 19), (8, 5, 3), (68, 25, 33), (64, 12, 16)])
-@pytest.mark.parametrize("m", [3, 4, 5, 12])
-def test_pcg_two_chebyshev_steps_per_pass(n, m):
-    """3D TMA path: the preconditioner's steps after the first two per pass (64 x 12
-    bricks, first step on the 72 x 14 halo region) against one per pass -- bitwise
-    identical, the same FMA-ordered update -- and against the oracle.  m = 3 (no
-    pair), 4 (one pair, the last), 5 (a pair and a last single step), 12; ragged
-    bricks in x, y and z, a grid smaller than one brick."""
-    p = case("heat3d_mixed", g_cheb=m, n=n)
-    rng = np.random.default_rng(65)
-    shape = tuple(reversed(n))
-    b = rng.standard_normal(shape)
-    x0 = b + 0.1 * rng.standard_normal(shape)
-    ref, ref_it = heat.Propagators(p).G(b, x0=x0)
-    got, its = {}, {}
-    with Ctx(p) as c:
-        for per_pass in (1, 2):
-            pr.parareal_set_option(c.ctx, pr.PR_OPT_G_CHEB_STEPS_PER_PASS, per_pass)
-            out = torch().empty(c.M, dtype=torch().float64, device="cuda")
-            its[per_pass] = pr.parareal_coarse(c.ctx, dev(b), dev(x0), out)
-            got[per_pass] = host(out)
-        with pytest.raises(pr.PararealError):
-            pr.parareal_set_option(c.ctx, pr.PR_OPT_G_CHEB_STEPS_PER_PASS, 3)
-    assert its[1] == its[2] and np.array_equal(got[1], got[2])
-    assert abs(its[2] - ref_it) <= 2, (its[2], ref_it)
-    assert rel_l2(got[2], ref) < 1e-12
-
-
 def test_pcg_vectorised_sync_parareal_parity():
     n = (132, 61)
     p = case("heat2d_explicit", tol=1e-9, g_cheb=8, n=n)
