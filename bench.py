@@ -46,7 +46,8 @@ WORKLOADS = {
                        "by the asynchronous persistent kernel (no injected delays) next to the "
                        "synchronous solve, tol 1e-6",
     "heat2d_explicit": "2D heat 1024x1024, N=64 slices, F=256 explicit 5-pt steps (dt=0.2h^2), "
-                       "G=1 implicit Euler step by CG (rtol 1e-10), FP64, sync Parareal, tol 1e-10",
+                       "G=1 implicit Euler step by FP64 CG (rtol 1e-10) preconditioned by 16 FP32 "
+                       "Chebyshev steps, FP64, sync Parareal, tol 1e-10",
     "heat3d_mixed": "3D heat 256^3, N=128 slices, F=64 explicit 7-pt steps (dt=0.15h^2), "
                     "G=implicit Euler by FP64 CG (rtol 1e-7) preconditioned by 12 FP32 Chebyshev "
                     "steps, FP32 fine / FP64 coarse vs plain FP64, sync, time to 1e-5",

@@ -27,7 +27,8 @@ pytestmark = pytest.mark.gpu
 
 
 def test_heat2d_bench_workload_sampled_parity():
-    """1024^2, N = 64, F = 256 explicit steps, CG rtol 1e-10, tol 1e-10 (the bench line)."""
+    """1024^2, N = 64, F = 256 explicit steps, coarse CG rtol 1e-10 preconditioned by
+    16 Chebyshev steps, tol 1e-10 (the 2D workload's launch configuration)."""
     p = preset("heat2d_explicit", "full")
     P = heat.Propagators(p)
     shape = tuple(reversed(p["n"]))
