@@ -921,13 +921,14 @@ def run_ours(args, world, rank, local):
     if is_mixed:
         tma = dim == 3 and p["n"][0] % 4 == 0 and p.get("kappa") is None
         nf = p["f_steps"]
-        # passes of one F: the first (FP64 in, FP32 out: 12 B per point) and the last
-        # (FP32 in, FP64 out: 12 B), the middle steps one per pass or, TMA-fed, two per
-        # pass (one read and one write of the FP32 state, 8 B per point per pass)
+        # passes of one F: the entry (FP64 in, FP32 out: 12 B per point; on the TMA path
+        # a conversion, otherwise the first step), the steps before the last one per
+        # pass or, TMA-fed, two per pass (one read and one write of the FP32 state, 8 B
+        # per point per pass), and the last step (FP32 in, FP64 out: 12 B)
         if nf == 1:
             passes, bytes_pt = 1, 16
         else:
-            mid = nf - 2
+            mid = nf - 1 if tma else nf - 2
             mid_passes = (mid // 2 + mid % 2) if (tma and args.f_per_pass == 2) else mid
             passes, bytes_pt = 2 + mid_passes, 24 + 8 * mid_passes
         fine_launches = sum(s["iterations"] for s in roof_stats) * passes
@@ -936,7 +937,8 @@ def run_ours(args, world, rank, local):
                 "unit": "GB/s", "traffic": None,
                 "kernel": (("step3d_tma2 (two TMA-fed FP32 steps per pass" if args.f_per_pass == 2
                             else "step3d_tma (TMA-fed FP32 steps") +
-                           "; first/last step step3d_v4 with FP64 I/O)" if tma else "step3d_v4<float>"),
+                           "; FP64 input converted by a streaming copy, last step step3d_v4 with "
+                           "FP64 output)" if tma else "step3d_v4<float>"),
                 "peak_kind": peak_kind,
                 "bytes_per_lup": bytes_pt / nf, "passes_per_F": passes}
         roof["frac"] = roof["achieved"] / roof["peak"]
