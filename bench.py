@@ -94,6 +94,12 @@ NCU_TRAFFIC_PER_LUP = {"heat2d_explicit": 1016.3e6 / (63 * 1048576),
                        # profiles/step3d_tma2_fp32_heat3d_256cubed_N4.md: 520.4 MB for one
                        # two-step pass over 4 x 256^3 points (2 updates each)
                        "heat3d_mixed": 520.4e6 / (2 * 4 * 256 ** 3)}
+# The coarse CG kernel's DRAM bytes over its algorithmic bytes (pcg_pass_costs), from
+# one ncu capture of every cg_kernel launch of a small run of the same workload
+# (profiles/pcg_cg_kernel_heat3d_256cubed_N4.md: 352.66 GB for 350.31 GB algorithmic,
+# 10 solves and 78 iterations at 256^3); traffic per launch = ratio x the bench's
+# algorithmic bytes per launch.
+NCU_COARSE_TRAFFIC_RATIO = {"heat3d_mixed": 352.66 / 350.31}
 
 
 def cost_model_sync(p, st, ms_per_solve):
@@ -794,7 +800,6 @@ def run_adjoint_async_workload(args, local):
 # operator scaled by 1/R_x): textbook CG d DADD + d DFMA for B p plus 5 DFMA (p.q,
 # x, r, r.r, p); single-reduction d + d for B r plus 6 DFMA (p, s, x, r, r.r, w.r).
 CG_OPS_PER_POINT = {("textbook", 2): 9, ("textbook", 3): 11, ("single", 2): 10, ("single", 3): 12}
-CG_L2_POINTS = 1 << 21   # the library's automatic choice: single-reduction up to here
 
 
 def fp64_peaks(pr, torch, sm_max_mhz):
@@ -815,6 +820,55 @@ def fp64_peaks(pr, torch, sm_max_mhz):
     except Exception as e:   # the probe is a measurement aid; the bench line stands without it
         out["probe_error"] = str(e)
     return out
+
+
+# Per-point cost of the passes of the vectorised Chebyshev-preconditioned coarse CG
+# (degree m >= 4, constant kappa): (HBM bytes, FP64 instructions).  Chebyshev steps
+# (FP32): the first reads f with its stencil and writes y_2 (8 B), the second
+# reads y_2 and f and writes y_3 (12 B), the middle ones read y_k, y_k-1, f and
+# write y_k+1 (16 B), the last also reads r in FP64 for r.z (24 B, one DFMA).
+# Direction pass: z (FP32) with its stencil, p, q in; p, q out (36 B; the scaled
+# operator 4 (2D) or 6 (3D) FP64 instructions, p, q, p.q one each).  Solution and
+# residual pass: x, p, r, q in; x, r, f out (52 B; x, r, r.r).  Per solve: the
+# start pass (x0 with its stencil, b in; r, f out: 28 B; the unscaled operator 5
+# or 7, b - Bx, r.r, b.b), the fused correction (x, v, w, lambda in; lambda, w
+# out: 48 B; the correction's add and subtract, the increment: 3), and the first
+# direction pass in place of a full one (z in; p, q out: 20 B; operator and p.q).
+# FP32 <-> FP64 conversions run on the integer pipe and count as neither.
+def pcg_pass_costs(dim, m):
+    op = 6 if dim == 3 else 4
+    it = [(8, 0), (12, 0)] + [(16, 0)] * (m - 4) + [(24, 1), (36, op + 3), (52, 3)]
+    solve = [(28, op + 4), (48, 3)]
+    first_dir = (20, op + 1)
+    return it, solve, first_dir
+
+
+def pcg_roofline(M, dim, m, cg_its, solves, t_coarse_ms, hbm_peak, peak_kind, fp64_gops):
+    """Coarse-phase roofline: each pass is bound by the larger of its HBM time and
+    its FP64-pipe time; the bound of the phase is the sum over its passes."""
+    it, solve, first_dir = pcg_pass_costs(dim, m)
+
+    def t_pass(c):   # seconds per point
+        return max(c[0] / (hbm_peak * 1e9), c[1] / (fp64_gops * 1e9))
+    t_it = sum(t_pass(c) for c in it)
+    t_solve = sum(t_pass(c) for c in solve) + t_pass(first_dir) - t_pass(it[-2])
+    t_bound = M * (cg_its * t_it + solves * t_solve)
+    per_it_b = sum(b for b, _ in it)
+    per_solve_b = sum(b for b, _ in solve) + first_dir[0] - it[-2][0]
+    gbytes = M * (cg_its * per_it_b + solves * per_solve_b)
+    achieved = gbytes / (t_coarse_ms / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+            "peak_kind": peak_kind, "frac": achieved / hbm_peak,
+            "bytes_per_point_per_iteration": per_it_b, "bytes_per_point_per_solve": per_solve_b,
+            "fp64_per_point_per_iteration": sum(f for _, f in it),
+            "fp64_peak_gops": fp64_gops,
+            "t_bound_ms": t_bound * 1e3, "frac_of_pass_roofline": t_bound * 1e3 / t_coarse_ms,
+            "pass_roofline_note": "per pass, the larger of HBM bytes / measured copy bandwidth "
+                                  "and FP64 instructions / probed DFMA rate, summed over the "
+                                  "passes, over the measured coarse-phase time",
+            "avg_launch_ms": t_coarse_ms / max(solves, 1),
+            "algorithmic_bytes_per_launch": gbytes / max(solves, 1),
+            "traffic": None}
 
 
 def run_ours(args, world, rank, local):
@@ -850,7 +904,9 @@ def run_ours(args, world, rank, local):
         code, st = pr.parareal_run_sync(ctx, lam)
         torch.cuda.synchronize()
         print(json.dumps({"profile": args.workload, "iterations": st.iterations,
-                          "launches": st.launches, "t_total_ms": st.t_total_ms}), flush=True)
+                          "launches": st.launches, "t_total_ms": st.t_total_ms,
+                          "cg_iterations": st.cg_iterations,
+                          "coarse_solves": st.coarse_solves}), flush=True)
         pr.parareal_destroy(ctx)
         return 0
 
@@ -982,8 +1038,7 @@ def run_ours(args, world, rank, local):
     # coarse sweep (the predictor and the corrections' CG solves): FP64 pipe
     roof_coarse = None
     if p.get("g_solver") != "thomas" and not args.g_cheb and p.get("kappa") is None:
-        rec = ("single" if args.g_cg == 2 or (args.g_cg == 0 and M <= CG_L2_POINTS)
-               else "textbook")
+        rec = "single" if args.g_cg == 2 else "textbook"
         ops_g = CG_OPS_PER_POINT[(rec, dim)] * cg_its * M
         roof_coarse = alu_roof(ops_g, t_coarse, "cg_kernel (%s CG recurrence)" % rec,
                                {"cg_iterations": cg_its,
@@ -996,24 +1051,20 @@ def run_ours(args, world, rank, local):
                        "cg_iterations": cg_its,
                        "us_per_cg_iteration": t_coarse * 1e3 / max(cg_its, 1)}
         vec = dim >= 2 and p.get("kappa") is None and p["n"][0] % 4 == 0
-        if args.g_cheb >= 3 and vec:
-            # algorithmic HBM bytes per point: per iteration the m - 1 FP32 Chebyshev
-            # passes (first 12 B: y_1 with its stencil, f, y_2 out; middle 16 B: y_k,
-            # y_k-1, f in, y_k+1 out; last 28 B: also r in and z out in FP64), the fused
-            # direction/operator pass (z with its stencil, p, q in; p, q out: 40 B) and
-            # the solution/residual pass (x, p, r, q in; x, r, f, y_1 out: 56 B); per
-            # solve the start pass (b, x0 in; x, r, f, y_1 out: 40 B) and the fused
-            # correction (x, v, w, lambda in; lambda, w out: 48 B)
-            m = args.g_cheb
-            per_it = 12 + 16 * (m - 3) + 28 + 40 + 56
-            solves = sum(s["coarse_solves"] for s in roof_stats)
-            gbytes = M * (cg_its * per_it + solves * 88)
-            roof_coarse.update({"bound": "hbm", "achieved": gbytes / (t_coarse / 1e3) / 1e9,
-                                "peak": hbm_peak, "unit": "GB/s", "peak_kind": peak_kind,
-                                "bytes_per_point_per_iteration": per_it,
-                                "bytes_per_point_per_solve": 88,
-                                "traffic": None})
-            roof_coarse["frac"] = roof_coarse["achieved"] / hbm_peak
+        if args.g_cheb >= 4 and vec:
+            roof_coarse.update(pcg_roofline(M, dim, args.g_cheb, cg_its,
+                                            sum(s["coarse_solves"] for s in roof_stats),
+                                            t_coarse, hbm_peak, peak_kind,
+                                            fpk.get("probe_dfma_gops") or fp64_peak))
+            ratio = NCU_COARSE_TRAFFIC_RATIO.get(args.workload)
+            if ratio:
+                roof_coarse["traffic"] = ratio * roof_coarse["algorithmic_bytes_per_launch"]
+    # the bench line's roofline is that of the kernel with the larger share of the solve
+    dominant = roof
+    if roof_coarse and roof_coarse.get("frac") is not None and t_coarse > t_fine:
+        dominant = dict(roof_coarse, share_of_solve=t_coarse / (t_fine + t_coarse))
+    else:
+        dominant = dict(roof, share_of_solve=t_fine / max(t_fine + t_coarse, 1e-9))
     out = {"metric": "fine GLUP/s", "value": value, "unit": "GLUP/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -1027,7 +1078,8 @@ def run_ours(args, world, rank, local):
            "predictor": {"cg_iterations": roof_stats[-1]["predictor_cg_iterations"],
                          "t_ms": roof_stats[-1]["t_predictor_ms"]},
            "cost_model": cost_model_sync(p, roof_stats[-1], roof_stats[-1]["t_total_ms"]),
-           "roofline": roof, "roofline_coarse": roof_coarse, "fp64_peak": fpk,
+           "roofline": dominant, "roofline_fine": roof, "roofline_coarse": roof_coarse,
+           "fp64_peak": fpk,
            "gpu_launches": launches}
     # GPU serial fine solve on the same problem (time-to-solution reference)
     sf = torch.empty_like(lam)

@@ -335,6 +335,17 @@ int parareal_coarse_noalloc(int dim, const int* n, double dT, const double* b_de
 int parareal_probe_fp64(int kind, long long iters, double* scratch_dev, double* ops_per_s_host,
                         long long* ops_host, void* cuda_stream);
 
+/* Conversion check (a test aid; the paper has no counterpart).  The coarse
+ * solver's vectorised passes convert between FP32 and FP64 with integer
+ * operations instead of the conversion instructions, which issue on the FP64
+ * pipe; this entry applies those conversions elementwise on the given stream:
+ * d_out_dev[i] = widen(f_in_dev[i]) (exact) and f_out_dev[i] =
+ * narrow(d_in_dev[i]) (round to nearest, ties to even), n elements, all four
+ * device buffers caller-owned.  Asynchronous.  PR_EINVAL for n < 0 or a NULL
+ * buffer with n > 0; PR_ECUDA when the launch fails. */
+int parareal_probe_convert(const float* f_in_dev, double* d_out_dev, const double* d_in_dev,
+                           float* f_out_dev, long long n, void* cuda_stream);
+
 void parareal_destroy(pr_ctx* ctx);
 const char* parareal_last_error(const pr_ctx* ctx);
 const char* parareal_version(void);

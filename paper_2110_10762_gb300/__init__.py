@@ -13,5 +13,5 @@ from .api import (PararealError, make_async_opts, make_problem, parareal_adjoint
                   parareal_adjoint_async,
                   parareal_coarse, parareal_coarse_noalloc, parareal_correct, parareal_create, parareal_destroy,
                   parareal_fine, parareal_last_error, parareal_run_async, parareal_run_sync,
-                  parareal_run_sync_host, parareal_serial_fine, parareal_set_problem, parareal_probe_fp64,
+                  parareal_run_sync_host, parareal_serial_fine, parareal_set_problem, parareal_probe_fp64, parareal_probe_convert,
                   parareal_set_option, parareal_slice_stats, parareal_version)

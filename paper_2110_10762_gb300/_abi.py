@@ -81,6 +81,8 @@ EXPORTS = {
                                           C.POINTER(C.c_int), C.c_void_p]),
     "parareal_probe_fp64": (C.c_int, [C.c_int, C.c_longlong, C.c_void_p, C.POINTER(C.c_double),
                                       C.POINTER(C.c_longlong), C.c_void_p]),
+    "parareal_probe_convert": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                         C.c_longlong, C.c_void_p]),
     "parareal_destroy": (None, [C.c_void_p]),
     "parareal_last_error": (C.c_char_p, [C.c_void_p]),
     "parareal_version": (C.c_char_p, []),

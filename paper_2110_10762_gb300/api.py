@@ -254,6 +254,27 @@ def parareal_probe_fp64(kind: int, iters: int = 1 << 16, stream=None):
     return rate.value, ops.value
 
 
+def parareal_probe_convert(f_in, d_in, stream=None):
+    """The library's integer-pipe conversions applied elementwise (see
+    include/parareal.h): returns (widen(f_in) as float64, narrow(d_in) as
+    float32) for two CUDA tensors of the same length."""
+    import torch
+    if f_in.dtype != torch.float32 or d_in.dtype != torch.float64 or f_in.numel() != d_in.numel():
+        raise ValueError("f_in must be float32 and d_in float64, of equal length")
+    f_in, d_in = f_in.contiguous(), d_in.contiguous()
+    d_out = torch.empty(f_in.numel(), dtype=torch.float64, device=f_in.device)
+    f_out = torch.empty(d_in.numel(), dtype=torch.float32, device=d_in.device)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    if not isinstance(stream, int):
+        stream = stream.cuda_stream
+    code = _lib().parareal_probe_convert(_ptr(f_in, False), _ptr(d_out), _ptr(d_in),
+                                         _ptr(f_out, False), int(f_in.numel()), stream)
+    if code != PR_OK:
+        raise PararealError(code, "parareal_probe_convert failed")
+    return d_out, f_out
+
+
 def parareal_destroy(ctx):
     if ctx:
         _lib().parareal_destroy(ctx)

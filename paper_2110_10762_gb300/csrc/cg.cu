@@ -167,24 +167,39 @@ __device__ __forceinline__ double cheb_step(const Geom& g, const ChebDev& ch, bo
 // y_{k+1} = y_k + d_k with d_{k-1} = y_k - y_{k-1}, is the same recurrence as
 //     y_{k+1} = y_k + c1 (y_k - y_{k-1}) + c2 (f - B y_k),      y_0 = 0,
 // which reads y_k (with its stencil), y_{k-1} and f and writes y_{k+1}: 16
-// bytes per point instead of 24.  A warp owns 128 consecutive x (one float4
-// per lane) of one row of the middle axis (y in 3D) and streams CV_ZC planes
-// of the slowest axis (z in 3D, y in 2D), carrying the previous, current and
-// next plane of y_k in registers; x-neighbours come from the adjacent lanes by
+// bytes per point instead of 24.  y_1 = f / c is never stored: the first step
+// (KIND 1) reads f with its stencil and scales every value by 1/c (8 bytes per
+// point), the second (KIND 2) forms y_1 from the f it reads anyway (12 bytes),
+// the later ones (KIND 0) read the stored y_{k-1};
+// the scaling is an uncontracted FP32 product, so the values are those a
+// stored y_1 would hold.  A warp owns 128 consecutive x (one float4 per lane)
+// of one row of the middle axis (y in 3D) and streams CV_ZC planes of the
+// slowest axis (z in 3D, y in 2D), carrying the previous, current and next
+// plane of y_k in registers; x-neighbours come from the adjacent lanes by
 // shuffles (the warp's two edge values by one scalar load each), middle-axis
-// neighbours by float4 loads.  The last step writes z = y_m in FP64 and
+// neighbours by float4 loads.  The last step's y_m is z, kept in FP32 (it is
+// an FP32 value; the CG passes read it exactly widened to FP64), and the step
 // returns this thread's part of r.z.
 constexpr int CV_ZC = 8;
 
 __device__ __forceinline__ float4 ldf4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 
-template <int DIM, bool FIRST, bool LAST>
+// FP32 <-> FP64 in the vectorised passes: integer-pipe conversions (a conversion
+// instruction would issue on the FP64 pipe, at the DFMA rate)
+__device__ __forceinline__ double f2d(float v) { return widen_f32(v); }
+__device__ __forceinline__ float d2f(double v) { return narrow_f64_rn(v); }
+
+__device__ __forceinline__ float4 mulf4(float4 v, float s) {
+  return make_float4(__fmul_rn(v.x, s), __fmul_rn(v.y, s), __fmul_rn(v.z, s), __fmul_rn(v.w, s));
+}
+
+template <int DIM, int KIND, bool LAST>
 __device__ __forceinline__ double cheb3_step(const Geom& g, const ChebDev& ch,
                                              const float* __restrict__ yk,
                                              const float* __restrict__ ykm,
                                              const float* __restrict__ f, float* __restrict__ yn,
-                                             double* __restrict__ z, const double* __restrict__ r,
-                                             float c1, float c2, int blk, int nblk) {
+                                             const double* __restrict__ r, float c1, float c2,
+                                             int blk, int nblk) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int wpb = blockDim.x >> 5;
@@ -200,7 +215,13 @@ __device__ __forceinline__ double cheb3_step(const Geom& g, const ChebDev& ch,
   const float c0 = ch.c0, rx = ch.rx;
   const float rm = DIM == 3 ? ch.ry : 0.f;           // middle-axis coupling
   const float rs = DIM == 3 ? ch.rz : ch.ry;         // streamed-axis coupling
+  const float ic = ch.inv_c;
   const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  // KIND 1 streams f itself, scaled to y_1 as it is loaded (its centre f is
+  // loaded again, from cache)
+  auto sc4 = [&](float4 v) { return KIND == 1 ? mulf4(v, ic) : v; };
+  auto sc1 = [&](float v) { return KIND == 1 ? __fmul_rn(v, ic) : v; };
+  const float* src = KIND == 1 ? f : yk;
   double acc = 0.0;
   for (long long j = gw; j < items; j += nw) {
     const int xc = (int)(j % XC);
@@ -213,19 +234,19 @@ __device__ __forceinline__ double cheb3_step(const Geom& g, const ChebDev& ch,
     const long long row = (DIM == 3 ? (long long)ym * nx : 0) + x;
     float4 prv = zero, cur = zero;
     if (act) {
-      if (s0 > 0) prv = ldf4(yk + (s0 - 1) * sst + row);
-      cur = ldf4(yk + s0 * sst + row);
+      if (s0 > 0) prv = sc4(ldf4(src + (s0 - 1) * sst + row));
+      cur = sc4(ldf4(src + s0 * sst + row));
     }
     for (int sl = s0; sl < s1; ++sl) {
       const long long o = sl * sst + row;
       float4 nxt = zero, mid = zero, fv = zero, pv = zero;
       float wv = 0.f, ev = 0.f;
       if (act) {
-        if (sl + 1 < ns) nxt = ldf4(yk + o + sst);
+        if (sl + 1 < ns) nxt = sc4(ldf4(src + o + sst));
         if (DIM == 3) {
-          if (ym > 0) mid = ldf4(yk + o - nx);
+          if (ym > 0) mid = sc4(ldf4(src + o - nx));
           if (ym + 1 < nm) {
-            const float4 q = ldf4(yk + o + nx);
+            const float4 q = sc4(ldf4(src + o + nx));
             mid.x += q.x;
             mid.y += q.y;
             mid.z += q.z;
@@ -233,9 +254,10 @@ __device__ __forceinline__ double cheb3_step(const Geom& g, const ChebDev& ch,
           }
         }
         fv = ldf4(f + o);
-        if (!FIRST) pv = ldf4(ykm + o);
-        if (lane == 0 && x > 0) wv = yk[o - 1];
-        if (lane == 31 && x + 4 < nx) ev = yk[o + 4];
+        if (KIND == 2) pv = mulf4(fv, ic);
+        if (KIND == 0) pv = ldf4(ykm + o);
+        if (lane == 0 && x > 0) wv = sc1(src[o - 1]);
+        if (lane == 31 && x + 4 < nx) ev = sc1(src[o + 4]);
       }
       const float wsh = __shfl_up_sync(FULL, cur.w, 1);
       const float esh = __shfl_down_sync(FULL, cur.x, 1);
@@ -254,19 +276,14 @@ __device__ __forceinline__ double cheb3_step(const Geom& g, const ChebDev& ch,
         out.w = cur.w + c1 * (cur.w - pv.w) + c2 * (fv.w - b3);
       }
       if (act) {
+        *reinterpret_cast<float4*>(yn + o) = out;
         if (LAST) {
-          const double2 z01 = make_double2(out.x, out.y), z23 = make_double2(out.z, out.w);
-          double2* zp = reinterpret_cast<double2*>(z + o);
-          zp[0] = z01;
-          zp[1] = z23;
           const double2* rp = reinterpret_cast<const double2*>(r + o);
           const double2 r01 = rp[0], r23 = rp[1];
-          acc = fma(r01.x, z01.x, acc);
-          acc = fma(r01.y, z01.y, acc);
-          acc = fma(r23.x, z23.x, acc);
-          acc = fma(r23.y, z23.y, acc);
-        } else {
-          *reinterpret_cast<float4*>(yn + o) = out;
+          acc = fma(r01.x, f2d(out.x), acc);
+          acc = fma(r01.y, f2d(out.y), acc);
+          acc = fma(r23.x, f2d(out.z), acc);
+          acc = fma(r23.y, f2d(out.w), acc);
         }
       }
       prv = cur;
@@ -277,7 +294,8 @@ __device__ __forceinline__ double cheb3_step(const Geom& g, const ChebDev& ch,
 }
 
 // TMA-fed three-term Chebyshev step (3D, constant kappa, nx % 4 == 0): the same
-// arithmetic as cheb3_step, with y_k staged through shared memory.  The group's
+// arithmetic and step kinds as cheb3_step, with y_k (f for the first step)
+// staged through shared memory.  The group's
 // blocks take 64 x 16 x CT_ZC bricks round-robin; for each brick one elected
 // thread issues cp.async.bulk.tensor loads of the 72 x 18 planes of y_k (x halo
 // 4 wide so that every load starts on a 16-byte boundary; the copy engine fills
@@ -302,11 +320,11 @@ struct ChebTma {
   bool dead;                 // a bounded wait expired (block-uniform)
 };
 
-template <bool FIRST, bool LAST>
+template <int KIND, bool LAST>
 __device__ __forceinline__ double cheb_tma_step(const Geom& g, const ChebDev& ch, const void* map,
                                                 const float* __restrict__ ykm,
                                                 const float* __restrict__ f,
-                                                float* __restrict__ yn, double* __restrict__ z,
+                                                float* __restrict__ yn,
                                                 const double* __restrict__ r, float c1, float c2,
                                                 int blk, int nblk, ChebTma& tm) {
   const int tid = threadIdx.x;
@@ -347,9 +365,10 @@ __device__ __forceinline__ double cheb_tma_step(const Geom& g, const ChebDev& ch
       const int L = zi - z0 + 1;
       const long long o = zi * plane + (long long)gy * g.nx + gx;
       float4 fv = make_float4(0.f, 0.f, 0.f, 0.f), pv = fv;
-      if (inside) {
+      if (inside && KIND != 1) {
         fv = ldf4(f + o);
-        if (!FIRST) pv = ldf4(ykm + o);
+        if (KIND == 2) pv = mulf4(fv, ch.inv_c);
+        else if (KIND == 0) pv = ldf4(ykm + o);
       }
       while (ok && waited <= L + 1) {
         const unsigned q = gl + waited;
@@ -364,12 +383,24 @@ __device__ __forceinline__ double cheb_tma_step(const Geom& g, const ChebDev& ch
         const float* Pm = tm.stage + ((gl + L - 1) % CT_ST) * CT_STRIDE;
         const float* Pc = tm.stage + ((gl + L) % CT_ST) * CT_STRIDE;
         const float* Pp = tm.stage + ((gl + L + 1) % CT_ST) * CT_STRIDE;
-        const float4 cur = *reinterpret_cast<const float4*>(Pc + c);
-        const float4 s4 = *reinterpret_cast<const float4*>(Pc + c - CT_PX);
-        const float4 n4 = *reinterpret_cast<const float4*>(Pc + c + CT_PX);
-        const float4 b4 = *reinterpret_cast<const float4*>(Pm + c);
-        const float4 f4 = *reinterpret_cast<const float4*>(Pp + c);
-        const float w = Pc[c - 1], e = Pc[c + 4];
+        float4 cur = *reinterpret_cast<const float4*>(Pc + c);
+        float4 s4 = *reinterpret_cast<const float4*>(Pc + c - CT_PX);
+        float4 n4 = *reinterpret_cast<const float4*>(Pc + c + CT_PX);
+        float4 b4 = *reinterpret_cast<const float4*>(Pm + c);
+        float4 f4 = *reinterpret_cast<const float4*>(Pp + c);
+        float w = Pc[c - 1], e = Pc[c + 4];
+        if (KIND == 1) {
+          // staged f: the centre is f itself, every stencil value is y_1 = f / c
+          const float ic = ch.inv_c;
+          fv = cur;
+          cur = mulf4(cur, ic);
+          s4 = mulf4(s4, ic);
+          n4 = mulf4(n4, ic);
+          b4 = mulf4(b4, ic);
+          f4 = mulf4(f4, ic);
+          w = __fmul_rn(w, ic);
+          e = __fmul_rn(e, ic);
+        }
         const float b0 = c0 * cur.x - rx * (w + cur.y) - ry * (s4.x + n4.x) - rz * (b4.x + f4.x);
         const float b1 = c0 * cur.y - rx * (cur.x + cur.z) - ry * (s4.y + n4.y) - rz * (b4.y + f4.y);
         const float b2 = c0 * cur.z - rx * (cur.y + cur.w) - ry * (s4.z + n4.z) - rz * (b4.z + f4.z);
@@ -379,19 +410,14 @@ __device__ __forceinline__ double cheb_tma_step(const Geom& g, const ChebDev& ch
         out.y = cur.y + c1 * (cur.y - pv.y) + c2 * (fv.y - b1);
         out.z = cur.z + c1 * (cur.z - pv.z) + c2 * (fv.z - b2);
         out.w = cur.w + c1 * (cur.w - pv.w) + c2 * (fv.w - b3);
+        *reinterpret_cast<float4*>(yn + o) = out;
         if (LAST) {
-          const double2 z01 = make_double2(out.x, out.y), z23 = make_double2(out.z, out.w);
-          double2* zp = reinterpret_cast<double2*>(z + o);
-          zp[0] = z01;
-          zp[1] = z23;
           const double2* rp = reinterpret_cast<const double2*>(r + o);
           const double2 r01 = rp[0], r23 = rp[1];
-          acc = fma(r01.x, z01.x, acc);
-          acc = fma(r01.y, z01.y, acc);
-          acc = fma(r23.x, z23.x, acc);
-          acc = fma(r23.y, z23.y, acc);
-        } else {
-          *reinterpret_cast<float4*>(yn + o) = out;
+          acc = fma(r01.x, f2d(out.x), acc);
+          acc = fma(r01.y, f2d(out.y), acc);
+          acc = fma(r23.x, f2d(out.z), acc);
+          acc = fma(r23.y, f2d(out.w), acc);
         }
       }
       // every thread is done with the stage of load L-1: refill it two planes ahead
@@ -419,48 +445,71 @@ __device__ __forceinline__ double cheb_tma_step(const Geom& g, const ChebDev& ch
   return acc;
 }
 
-// Steps k = 1..m-1 of the vectorised preconditioner: y_1 = f / c is in ring
-// slot 1 (written with f by the pass that updated r), y_k in slot k % 3.
+// Steps k = 1..m-1 of the vectorised preconditioner: y_1 = f / c is formed from
+// f (never stored), y_k for k >= 2 is in ring slot k % 3, and z = y_m ends in
+// slot m % 3.  Tensor maps (3D): slot q at tmaps + 128 q, f at tmaps + 384.
+__device__ __forceinline__ float* cheb_slot(const ChebDev& ch, int s) {
+  return s == 0 ? ch.y : s == 1 ? ch.d0 : ch.d1;
+}
+
 template <int DIM>
 __device__ __forceinline__ double cheb3_dispatch(const Geom& g, const ChebDev& ch,
                                                  const double* __restrict__ r, int kk, int blk,
                                                  int nblk, ChebTma& tm) {
   const int sk = kk % 3;
   const float c1 = ch.c1[kk], c2 = ch.c2[kk];
-  const float* yk = sk == 0 ? ch.y : sk == 1 ? ch.d0 : ch.d1;
-  const float* ykm = sk == 0 ? ch.d1 : sk == 1 ? ch.y : ch.d0;
-  float* yn = sk == 0 ? ch.d0 : sk == 1 ? ch.d1 : ch.y;
+  const float* yk = cheb_slot(ch, sk);
+  const float* ykm = cheb_slot(ch, (kk + 2) % 3);
+  float* yn = cheb_slot(ch, (kk + 1) % 3);
   const bool last = kk == ch.m - 1;
+  const float* f = ch.res;
   if (DIM == 3 && ch.tmaps) {
     if (tm.dead) return 0.0;
-    const void* map = ch.tmaps + 128 * sk;
     if (kk == 1) {
-      if (last) return cheb_tma_step<true, true>(g, ch, map, ykm, ch.res, yn, ch.z, r, c1, c2, blk, nblk, tm);
-      return cheb_tma_step<true, false>(g, ch, map, ykm, ch.res, yn, ch.z, r, c1, c2, blk, nblk, tm);
+      const void* map = ch.tmaps + 128 * 3;
+      if (last) return cheb_tma_step<1, true>(g, ch, map, ykm, f, yn, r, c1, c2, blk, nblk, tm);
+      return cheb_tma_step<1, false>(g, ch, map, ykm, f, yn, r, c1, c2, blk, nblk, tm);
     }
-    if (last) return cheb_tma_step<false, true>(g, ch, map, ykm, ch.res, yn, ch.z, r, c1, c2, blk, nblk, tm);
-    return cheb_tma_step<false, false>(g, ch, map, ykm, ch.res, yn, ch.z, r, c1, c2, blk, nblk, tm);
+    const void* map = ch.tmaps + 128 * sk;
+    if (kk == 2) {
+      if (last) return cheb_tma_step<2, true>(g, ch, map, ykm, f, yn, r, c1, c2, blk, nblk, tm);
+      return cheb_tma_step<2, false>(g, ch, map, ykm, f, yn, r, c1, c2, blk, nblk, tm);
+    }
+    if (last) return cheb_tma_step<0, true>(g, ch, map, ykm, f, yn, r, c1, c2, blk, nblk, tm);
+    return cheb_tma_step<0, false>(g, ch, map, ykm, f, yn, r, c1, c2, blk, nblk, tm);
   }
   if (kk == 1) {
-    if (last) return cheb3_step<DIM, true, true>(g, ch, yk, ykm, ch.res, yn, ch.z, r, c1, c2, blk, nblk);
-    return cheb3_step<DIM, true, false>(g, ch, yk, ykm, ch.res, yn, ch.z, r, c1, c2, blk, nblk);
+    if (last) return cheb3_step<DIM, 1, true>(g, ch, yk, ykm, f, yn, r, c1, c2, blk, nblk);
+    return cheb3_step<DIM, 1, false>(g, ch, yk, ykm, f, yn, r, c1, c2, blk, nblk);
   }
-  if (last) return cheb3_step<DIM, false, true>(g, ch, yk, ykm, ch.res, yn, ch.z, r, c1, c2, blk, nblk);
-  return cheb3_step<DIM, false, false>(g, ch, yk, ykm, ch.res, yn, ch.z, r, c1, c2, blk, nblk);
+  if (kk == 2) {
+    if (last) return cheb3_step<DIM, 2, true>(g, ch, yk, ykm, f, yn, r, c1, c2, blk, nblk);
+    return cheb3_step<DIM, 2, false>(g, ch, yk, ykm, f, yn, r, c1, c2, blk, nblk);
+  }
+  if (last) return cheb3_step<DIM, 0, true>(g, ch, yk, ykm, f, yn, r, c1, c2, blk, nblk);
+  return cheb3_step<DIM, 0, false>(g, ch, yk, ykm, f, yn, r, c1, c2, blk, nblk);
 }
 
 // ---- vectorised FP64 passes of the preconditioned CG (constant kappa, dim >= 2,
-// nx % 4 == 0).  A warp owns 64 consecutive x (one double2 per lane) of one row
+// nx % 4 == 0).  A warp owns 64 consecutive x (two values per lane) of one row
 // of the middle axis (y in 3D) and streams CV_ZC planes of the slowest axis,
-// carrying the previous, current and next plane of the stencil operand in
-// registers; x-neighbours come by shuffles (the warp's edge values by one load
-// each), middle-axis neighbours by double2 loads.  fn(o, cur, w, e, mid, bf) is
-// called for every lane that owns points: o = offset of its first point, cur =
-// its two values, w / e = the west neighbour of the first and the east
-// neighbour of the second, mid = the sum of the middle-axis neighbours (3D), bf
-// = the sum of the streamed-axis neighbours.
-template <int DIM, class Fn>
-__device__ __forceinline__ void stream64(const Geom& g, const double* __restrict__ u, int blk,
+// carrying the previous, current and next plane of the stencil operand u
+// (FP64, or FP32 widened exactly) in registers; x-neighbours come by shuffles
+// (the warp's edge values by one load each), middle-axis neighbours by pair
+// loads.  fn(o, cur, w, e, mid, bf) is called for every lane that owns points:
+// o = offset of its first point, cur = its two values, w / e = the west
+// neighbour of the first and the east neighbour of the second, mid = the sum of
+// the middle-axis neighbours (3D), bf = the sum of the streamed-axis neighbours.
+__device__ __forceinline__ double2 ld2(const double* p) { return *reinterpret_cast<const double2*>(p); }
+__device__ __forceinline__ double2 ld2(const float* p) {
+  const float2 v = *reinterpret_cast<const float2*>(p);
+  return make_double2(f2d(v.x), f2d(v.y));
+}
+__device__ __forceinline__ double ld1(const double* p) { return *p; }
+__device__ __forceinline__ double ld1(const float* p) { return f2d(*p); }
+
+template <int DIM, class T, class Fn>
+__device__ __forceinline__ void stream64(const Geom& g, const T* __restrict__ u, int blk,
                                          int nblk, Fn&& fn) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
@@ -486,25 +535,25 @@ __device__ __forceinline__ void stream64(const Geom& g, const double* __restrict
     const long long row = (DIM == 3 ? (long long)ym * nx : 0) + x;
     double2 prv = zero, cur = zero;
     if (act) {
-      if (s0 > 0) prv = *reinterpret_cast<const double2*>(u + (s0 - 1) * sst + row);
-      cur = *reinterpret_cast<const double2*>(u + s0 * sst + row);
+      if (s0 > 0) prv = ld2(u + (s0 - 1) * sst + row);
+      cur = ld2(u + s0 * sst + row);
     }
     for (int sl = s0; sl < s1; ++sl) {
       const long long o = sl * sst + row;
       double2 nxt = zero, mid = zero;
       double wv = 0.0, ev = 0.0;
       if (act) {
-        if (sl + 1 < ns) nxt = *reinterpret_cast<const double2*>(u + o + sst);
+        if (sl + 1 < ns) nxt = ld2(u + o + sst);
         if (DIM == 3) {
-          if (ym > 0) mid = *reinterpret_cast<const double2*>(u + o - nx);
+          if (ym > 0) mid = ld2(u + o - nx);
           if (ym + 1 < nm) {
-            const double2 q = *reinterpret_cast<const double2*>(u + o + nx);
+            const double2 q = ld2(u + o + nx);
             mid.x += q.x;
             mid.y += q.y;
           }
         }
-        if (lane == 0 && x > 0) wv = u[o - 1];
-        if (lane == 31 && x + 2 < nx) ev = u[o + 2];
+        if (lane == 0 && x > 0) wv = ld1(u + o - 1);
+        if (lane == 31 && x + 2 < nx) ev = ld1(u + o + 2);
       }
       const double wsh = __shfl_up_sync(FULL, cur.y, 1);
       const double esh = __shfl_down_sync(FULL, cur.x, 1);
@@ -547,8 +596,9 @@ __device__ __forceinline__ double gop_pt(const StencilConst& k, double u, double
   return r;
 }
 
-// Start of the preconditioned CG on the vectorised path: r = b - B x0, x = x0,
-// f = FP32(r), y_1 = f / c (ring slot 1); returns the partial r.r and b.b.
+// Start of the preconditioned CG on the vectorised path: r = b - B x0 and
+// f = FP32(r); returns the partial r.r and b.b.  x is read from x0 by the first
+// solution update (pcg_xr_vec), and y_1 = f / c is formed by the first step.
 template <int DIM>
 __device__ __forceinline__ void pcg_setup_vec(const CgDev& a, double& rr, double& bb, int blk,
                                               int nblk) {
@@ -561,11 +611,9 @@ __device__ __forceinline__ void pcg_setup_vec(const CgDev& a, double& rr, double
                   const double2 b = *reinterpret_cast<const double2*>(a.b + o);
                   const double r0 = b.x - gop_pt<DIM>(k, c.x, w, c.y, mid.x, bf.x);
                   const double r1 = b.y - gop_pt<DIM>(k, c.y, c.x, e, mid.y, bf.y);
-                  *reinterpret_cast<double2*>(ws.x + o) = c;
                   *reinterpret_cast<double2*>(ws.r + o) = make_double2(r0, r1);
-                  const float f0 = static_cast<float>(r0), f1 = static_cast<float>(r1);
+                  const float f0 = d2f(r0), f1 = d2f(r1);
                   *reinterpret_cast<float2*>(ch.res + o) = make_float2(f0, f1);
-                  *reinterpret_cast<float2*>(ch.d0 + o) = make_float2(f0 * ch.inv_c, f1 * ch.inv_c);
                   srr = fma(r0, r0, fma(r1, r1, srr));
                   sbb = fma(b.x, b.x, fma(b.y, b.y, sbb));
                 });
@@ -575,14 +623,15 @@ __device__ __forceinline__ void pcg_setup_vec(const CgDev& a, double& rr, double
 
 // Direction update fused with the operator on the vectorised path:
 //   p = z + beta p,   q = B' z + beta q   (= B' p, the operator being linear),
-// one pass over z (with its stencil), p and q; returns the partial p.q.  On the
-// first iteration p = z and q = B' z.
+// one pass over z (FP32, with its stencil), p and q; returns the partial p.q.
+// On the first iteration p = z and q = B' z.
 template <int DIM>
-__device__ __forceinline__ double pcg_pq_vec(const CgDev& a, const StencilConst& ks, double beta,
-                                             bool first, int blk, int nblk) {
+__device__ __forceinline__ double pcg_pq_vec(const CgDev& a, const float* __restrict__ z,
+                                             const StencilConst& ks, double beta, bool first,
+                                             int blk, int nblk) {
   const CgWork& ws = a.ws;
   double acc = 0.0;
-  stream64<DIM>(a.g, a.ch.z, blk, nblk,
+  stream64<DIM>(a.g, z, blk, nblk,
                 [&](long long o, double2 c, double w, double e, double2 mid, double2 bf) {
                   const double q0 = bop<DIM>(ks, c.x, w, c.y, mid.x, bf.x);
                   const double q1 = bop<DIM>(ks, c.y, c.x, e, mid.y, bf.y);
@@ -600,28 +649,27 @@ __device__ __forceinline__ double pcg_pq_vec(const CgDev& a, const StencilConst&
   return acc;
 }
 
-// x += (alpha sc) p, r -= alpha q, f = FP32(r), y_1 = f / c on the vectorised path,
-// two points per thread and two pairs in flight per trip; returns the partial r.r.
-__device__ __forceinline__ double pcg_x_vec(const CgDev& a, double alpha, double sc, int blk,
-                                            int nblk) {
+// x = xs + (alpha sc) p, r -= alpha q, f = FP32(r) on the vectorised path (xs is x0
+// on the first iteration, the workspace x after it), two points per thread and two
+// pairs in flight per trip; returns the partial r.r.
+__device__ __forceinline__ double pcg_xr_vec(const CgDev& a, double alpha, double ax,
+                                             const double* __restrict__ xs, int blk, int nblk) {
   const CgWork& ws = a.ws;
   const ChebDev& ch = a.ch;
   const long long P = a.g.M / 2;  // pairs (M is even on this path)
   const long long t0 = blk * (long long)blockDim.x + threadIdx.x;
   const long long nt = (long long)nblk * blockDim.x;
-  const double ax = alpha * sc;
   double s0 = 0.0, s1 = 0.0;
   auto one = [&](long long i, double& acc) {
-    const double2 x = reinterpret_cast<const double2*>(ws.x)[i];
+    const double2 x = reinterpret_cast<const double2*>(xs)[i];
     const double2 p = reinterpret_cast<const double2*>(ws.p)[i];
     const double2 r = reinterpret_cast<const double2*>(ws.r)[i];
     const double2 q = reinterpret_cast<const double2*>(ws.q)[i];
     const double r0 = fma(-alpha, q.x, r.x), r1 = fma(-alpha, q.y, r.y);
     reinterpret_cast<double2*>(ws.x)[i] = make_double2(fma(ax, p.x, x.x), fma(ax, p.y, x.y));
     reinterpret_cast<double2*>(ws.r)[i] = make_double2(r0, r1);
-    const float f0 = static_cast<float>(r0), f1 = static_cast<float>(r1);
+    const float f0 = d2f(r0), f1 = d2f(r1);
     reinterpret_cast<float2*>(ch.res)[i] = make_float2(f0, f1);
-    reinterpret_cast<float2*>(ch.d0)[i] = make_float2(f0 * ch.inv_c, f1 * ch.inv_c);
     acc = fma(r0, r0, fma(r1, r1, acc));
   };
   long long i = t0;
@@ -639,7 +687,9 @@ __device__ __forceinline__ double pcg_x_vec(const CgDev& a, double alpha, double
 // y = d_0 (reduction); m - 1 Chebyshev steps
 //   res -= B d_{k-1},  d_k = rho_k rho_{k-1} d_{k-1} + (2 rho_k / e) res,  y += d_k
 // (one grid barrier each; the last one writes z = y and reduces r.z); then
-// p = z + beta p.
+// p = z + beta p.  The vectorised path uses the three-term steps above and fuses
+// q = B' z + beta q into the direction update; its x lives in x0 until the
+// first solution update.
 __device__ int pcg_core(const CgDev& a, int nblk, int blk) {
   const Geom& g = a.g;
   const ChebDev& ch = a.ch;
@@ -670,7 +720,7 @@ __device__ int pcg_core(const CgDev& a, int nblk, int blk) {
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       // the tensor maps were written to global memory before the launch
-      for (int q = 0; q < 3; ++q)
+      for (int q = 0; q < 4; ++q)
         asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(ch.tmaps + 128 * q)
                      : "memory");
     }
@@ -753,9 +803,11 @@ __device__ int pcg_core(const CgDev& a, int nblk, int blk) {
       }
     }
     if (ch.vec) {
-      // ---- p = z + beta p and q = B' z + beta q in one pass, p.q
-      const double v[1] = {g.dim == 3 ? pcg_pq_vec<3>(a, ks, beta, it == 0, blk, nblk)
-                                      : pcg_pq_vec<2>(a, ks, beta, it == 0, blk, nblk)};
+      // ---- p = z + beta p and q = B' z + beta q in one pass, p.q (z = y_m is the
+      // FP32 ring slot m % 3)
+      const float* zf = cheb_slot(ch, ch.m % 3);
+      const double v[1] = {g.dim == 3 ? pcg_pq_vec<3>(a, zf, ks, beta, it == 0, blk, nblk)
+                                      : pcg_pq_vec<2>(a, zf, ks, beta, it == 0, blk, nblk)};
       block_sum<1>(v, part(), blk);
     } else {
       // ---- p = z + beta p (p = z on the first iteration)
@@ -773,7 +825,7 @@ __device__ int pcg_core(const CgDev& a, int nblk, int blk) {
     // ---- x, r, r.r; start the next preconditioner application
     double s0 = 0.0;
     if (ch.vec) {
-      s0 = pcg_x_vec(a, alpha, sc, blk, nblk);
+      s0 = pcg_xr_vec(a, alpha, alpha * sc, it == 0 ? a.x0 : ws.x, blk, nblk);
     } else {
       for (long long i = t0; i < M; i += nt) {
         const double ri = fma(-alpha, ws.q[i], ws.r[i]);
@@ -814,23 +866,12 @@ __device__ int pcg_core(const CgDev& a, int nblk, int blk) {
 // (Chebyshev-preconditioned).
 enum { CG_TEXTBOOK = 0, CG_SINGLE = 1, CG_CHEB = 2 };
 
-template <int MINB, int ALG>
-__global__ void __launch_bounds__(CG_THREADS, MINB) cg_kernel(CgDev a) {
+// Epilogue of a coarse solve, the solution x in hand: the plain or predictor
+// stores, or the fused correction of Algorithm 1 with its increment.
+__device__ __forceinline__ void cg_epilogue(const CgDev& a, const double* __restrict__ x) {
   const long long M = a.g.M;
   const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long nt = (long long)gridDim.x * blockDim.x;
-  if (a.mode == CG_CORRECT && t0 == 0) *a.delta = 0ull;
-  int it;
-  if constexpr (ALG == CG_CHEB)
-    it = pcg_core(a, gridDim.x, blockIdx.x);
-  else if constexpr (ALG == CG_SINGLE)
-    it = cg1_core(a.g, a.k, a.var != 0, a.gv, a.b, a.x0, a.rtol, a.maxit, a.ws, GridBarrier{},
-                  gridDim.x, blockIdx.x);
-  else
-    it = cg_core(a.g, a.k, a.var != 0, a.gv, a.b, a.x0, a.rtol, a.maxit, a.ws, GridBarrier{},
-                 gridDim.x, blockIdx.x);
-  // epilogue (x is final in the workspace)
-  const double* x = a.ws.x;
   if (a.mode == CG_PLAIN) {
     for (long long i = t0; i < M; i += nt) a.out[i] = x[i];
   } else if (a.mode == CG_PREDICTOR) {
@@ -870,6 +911,26 @@ __global__ void __launch_bounds__(CG_THREADS, MINB) cg_kernel(CgDev a) {
     }
     dmax = warp_max_u64(dmax);
     if ((threadIdx.x & 31) == 0 && dmax) atomicMax(a.delta, dmax);
+  }
+}
+
+template <int MINB, int ALG>
+__global__ void __launch_bounds__(CG_THREADS, MINB) cg_kernel(CgDev a) {
+  const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (a.mode == CG_CORRECT && t0 == 0) *a.delta = 0ull;
+  int it;
+  if constexpr (ALG == CG_CHEB) {
+    it = pcg_core(a, gridDim.x, blockIdx.x);
+    // vectorised path: x is x0 until the first solution update
+    cg_epilogue(a, a.ch.vec && it <= 0 ? a.x0 : a.ws.x);
+  } else {
+    if constexpr (ALG == CG_SINGLE)
+      it = cg1_core(a.g, a.k, a.var != 0, a.gv, a.b, a.x0, a.rtol, a.maxit, a.ws, GridBarrier{},
+                    gridDim.x, blockIdx.x);
+    else
+      it = cg_core(a.g, a.k, a.var != 0, a.gv, a.b, a.x0, a.rtol, a.maxit, a.ws, GridBarrier{},
+                   gridDim.x, blockIdx.x);
+    cg_epilogue(a, a.ws.x);
   }
   if (t0 == 0) *a.iters = it;
 }
@@ -1095,14 +1156,15 @@ cudaError_t cheb_alloc(pr_ctx* c) {
   if (e == cudaSuccess) e = cudaMalloc(&c->cheb_err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemsetAsync(c->cheb_err, 0, sizeof(int), c->stream);
   // 3D constant kappa with nx % 4 == 0: tensor maps of the three ring vectors
-  // (y, d0, d1 after the FP32 right-hand side f) for the TMA-fed steps; the
-  // steps fall back to plain vector loads when encoding is not possible
+  // (y, d0, d1, stored after the FP32 right-hand side f) and of f itself for the
+  // TMA-fed steps; the steps fall back to plain vector loads when encoding is
+  // not possible
   if (e == cudaSuccess && g.dim == 3 && !c->var_kappa && g.nx % 4 == 0) {
-    unsigned char maps[3 * 128];
+    unsigned char maps[4 * 128];
     bool ok = true;
-    for (int q = 0; q < 3 && ok; ++q)
-      ok = encode_f32_3d_map(maps + 128 * q, c->cheb_f32 + (size_t)(q + 1) * g.M, g.nx, g.ny, g.nz,
-                             CT_PX, CT_PY);
+    for (int q = 0; q < 4 && ok; ++q)
+      ok = encode_f32_3d_map(maps + 128 * q, c->cheb_f32 + (size_t)((q + 1) % 4) * g.M, g.nx, g.ny,
+                             g.nz, CT_PX, CT_PY);
     if (ok && cudaMalloc(&c->cheb_tmaps, sizeof maps) == cudaSuccess) {
       e = cudaMemcpyAsync(c->cheb_tmaps, maps, sizeof maps, cudaMemcpyHostToDevice, c->stream);
       if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);

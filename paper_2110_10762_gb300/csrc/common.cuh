@@ -121,7 +121,7 @@ struct pr_ctx {
   double g_lo = 0, g_hi = 0; // spectrum bounds of I + dT A
   double* cheb_z = nullptr;  // preconditioned residual (M)
   float* cheb_f32 = nullptr; // FP32 Chebyshev vectors (4 M)
-  void* cheb_tmaps = nullptr; // 3D: tensor maps of the three ring vectors (3 x 128 B, device)
+  void* cheb_tmaps = nullptr; // 3D: tensor maps of the three ring vectors and f (4 x 128 B, device)
   int* cheb_err = nullptr;   // 3D TMA-fed steps: 1 after a bounded wait expired
   // pipelined driver resources (created lazily)
   cudaStream_t s_sweep = nullptr, s_fine = nullptr;

@@ -9,6 +9,7 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "device.cuh"
 
 namespace pr {
 namespace {
@@ -37,8 +38,33 @@ __global__ void __launch_bounds__(PROBE_THREADS) fp64_probe_kernel(double* out, 
   if (!isfinite(s)) out[0] = s;
 }
 
+// The integer-pipe conversions of the coarse solver applied elementwise, so that
+// a test can compare them with the hardware conversions.
+__global__ void convert_check_kernel(const float* __restrict__ f_in, double* __restrict__ d_out,
+                                     const double* __restrict__ d_in, float* __restrict__ f_out,
+                                     long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    d_out[i] = widen_f32(f_in[i]);
+    f_out[i] = narrow_f64_rn(d_in[i]);
+  }
+}
+
 }  // namespace
 }  // namespace pr
+
+extern "C" int parareal_probe_convert(const float* f_in_dev, double* d_out_dev,
+                                      const double* d_in_dev, float* f_out_dev, long long n,
+                                      void* cuda_stream) {
+  using namespace pr;
+  if (n < 0 || (n > 0 && (!f_in_dev || !d_out_dev || !d_in_dev || !f_out_dev))) return PR_EINVAL;
+  if (n == 0) return PR_OK;
+  const long long want = (n + 255) / 256;
+  const int blocks = (int)(want < 4096 ? want : 4096);
+  convert_check_kernel<<<blocks, 256, 0, (cudaStream_t)cuda_stream>>>(f_in_dev, d_out_dev, d_in_dev,
+                                                                        f_out_dev, n);
+  return cudaGetLastError() == cudaSuccess ? PR_OK : PR_ECUDA;
+}
 
 extern "C" int parareal_probe_fp64(int kind, long long iters, double* scratch_dev,
                                    double* ops_per_s_host, long long* ops_host,
