@@ -14,6 +14,7 @@
 #include <cmath>
 
 #include "common.cuh"
+#include "convert.cuh"
 
 namespace pr {
 
@@ -157,16 +158,19 @@ constexpr int V4Z = 16;  // z planes per thread
 __device__ __forceinline__ float4 load4(const float* p) {
   return __ldg(reinterpret_cast<const float4*>(p));
 }
+// FP64 <-> FP32 at the ends of the FP32 steps by the integer-pipe conversions
+// (a conversion instruction issues on the FP64 pipe at the DFMA rate)
 __device__ __forceinline__ float4 load4(const double* p) {
   const double2 a = __ldg(reinterpret_cast<const double2*>(p));
   const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
-  return make_float4(static_cast<float>(a.x), static_cast<float>(a.y), static_cast<float>(b.x),
-                     static_cast<float>(b.y));
+  return make_float4(narrow_f64_rn(a.x), narrow_f64_rn(a.y), narrow_f64_rn(b.x), narrow_f64_rn(b.y));
 }
+__device__ __forceinline__ float to_f32(float v) { return v; }
+__device__ __forceinline__ float to_f32(double v) { return narrow_f64_rn(v); }
 __device__ __forceinline__ void store4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
 __device__ __forceinline__ void store4(double* p, float4 v) {
-  reinterpret_cast<double2*>(p)[0] = make_double2(v.x, v.y);
-  reinterpret_cast<double2*>(p)[1] = make_double2(v.z, v.w);
+  reinterpret_cast<double2*>(p)[0] = make_double2(widen_f32(v.x), widen_f32(v.y));
+  reinterpret_cast<double2*>(p)[1] = make_double2(widen_f32(v.z), widen_f32(v.w));
 }
 __device__ __forceinline__ float4 zero4() { return make_float4(0.f, 0.f, 0.f, 0.f); }
 
@@ -204,8 +208,8 @@ __global__ void __launch_bounds__(V4X* V4Y) step3d_v4(const Tin* __restrict__ in
     }
     float w = __shfl_up_sync(0xffffffffu, cur.w, 1, V4X);
     float e = __shfl_down_sync(0xffffffffu, cur.x, 1, V4X);
-    if (tx == 0) w = (valid && x4 > 0) ? static_cast<float>(__ldg(u + p - 1)) : 0.f;
-    if (tx == V4X - 1 || x4 + 4 >= nx) e = (valid && x4 + 4 < nx) ? static_cast<float>(__ldg(u + p + 4)) : 0.f;
+    if (tx == 0) w = (valid && x4 > 0) ? to_f32(__ldg(u + p - 1)) : 0.f;
+    if (tx == V4X - 1 || x4 + 4 >= nx) e = (valid && x4 + 4 < nx) ? to_f32(__ldg(u + p + 4)) : 0.f;
     float4 r;
     if (!VAR) {
       r.x = c0 * cur.x + rx * (w + cur.y) + ry * (s.x + n.x) + rz * (b.x + f.x);
@@ -401,7 +405,8 @@ __global__ void to_float_kernel(const double* __restrict__ a, float* __restrict_
 }
 
 // FP64 -> FP32 copy of n4 groups of four values (32 bytes in, 16 out per thread and
-// trip, two groups in flight): the entry of the TMA-fed FP32 steps.
+// trip, two groups in flight; integer-pipe rounding): the entry of the TMA-fed
+// FP32 steps.
 __global__ void to_float4_kernel(const double* __restrict__ a, float* __restrict__ b, long long n4) {
   const long long nt = (long long)gridDim.x * blockDim.x;
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -409,17 +414,17 @@ __global__ void to_float4_kernel(const double* __restrict__ a, float* __restrict
     const double2* p = reinterpret_cast<const double2*>(a) + 2 * i;
     const double2* q = reinterpret_cast<const double2*>(a) + 2 * (i + nt);
     const double2 p0 = p[0], p1 = p[1], q0 = q[0], q1 = q[1];
-    reinterpret_cast<float4*>(b)[i] = make_float4(static_cast<float>(p0.x), static_cast<float>(p0.y),
-                                                  static_cast<float>(p1.x), static_cast<float>(p1.y));
+    reinterpret_cast<float4*>(b)[i] = make_float4(narrow_f64_rn(p0.x), narrow_f64_rn(p0.y),
+                                                  narrow_f64_rn(p1.x), narrow_f64_rn(p1.y));
     reinterpret_cast<float4*>(b)[i + nt] =
-        make_float4(static_cast<float>(q0.x), static_cast<float>(q0.y), static_cast<float>(q1.x),
-                    static_cast<float>(q1.y));
+        make_float4(narrow_f64_rn(q0.x), narrow_f64_rn(q0.y), narrow_f64_rn(q1.x),
+                    narrow_f64_rn(q1.y));
   }
   if (i < n4) {
     const double2* p = reinterpret_cast<const double2*>(a) + 2 * i;
     const double2 p0 = p[0], p1 = p[1];
-    reinterpret_cast<float4*>(b)[i] = make_float4(static_cast<float>(p0.x), static_cast<float>(p0.y),
-                                                  static_cast<float>(p1.x), static_cast<float>(p1.y));
+    reinterpret_cast<float4*>(b)[i] = make_float4(narrow_f64_rn(p0.x), narrow_f64_rn(p0.y),
+                                                  narrow_f64_rn(p1.x), narrow_f64_rn(p1.y));
   }
 }
 
