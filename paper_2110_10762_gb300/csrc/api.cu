@@ -557,7 +557,7 @@ int parareal_run_sync(pr_ctx* c, double* lam, pr_stats* st) {
           PR_CUDA(c, vec_copy(c, wi, c->cg_x, M));
           S.launches += 3;
         } else {
-          S.launches += 1;
+          S.launches += cg_solve_launches(CG_CORRECT);
           CgArgs a{};
           a.b = lp;
           a.x0 = wi;

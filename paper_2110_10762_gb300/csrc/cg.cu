@@ -296,7 +296,7 @@ __device__ __forceinline__ double cheb3_step(const Geom& g, const ChebDev& ch,
 // TMA-fed three-term Chebyshev step (3D, constant kappa, nx % 4 == 0): the same
 // arithmetic and step kinds as cheb3_step, with y_k (f for the first step)
 // staged through shared memory.  The group's
-// blocks take 64 x 16 x CT_ZC bricks round-robin; for each brick one elected
+// blocks take 64 x 16 x (13-16) bricks round-robin; for each brick one elected
 // thread issues cp.async.bulk.tensor loads of the 72 x 18 planes of y_k (x halo
 // 4 wide so that every load starts on a 16-byte boundary; the copy engine fills
 // zeros outside the grid, the Dirichlet values) into a CT_ST-stage ring, each
@@ -307,7 +307,7 @@ __device__ __forceinline__ double cheb3_step(const Geom& g, const ChebDev& ch,
 // load is waited before the brick ends.  A wait that expires marks the block
 // dead (it drains its loads, sets ch.err and skips all later TMA work; the
 // solve is reported as failed).
-constexpr int CT_TX = 64, CT_TY = 16, CT_ZC = 16, CT_ST = 4;
+constexpr int CT_TX = 64, CT_TY = 16, CT_ST = 4;
 constexpr int CT_PX = CT_TX + 8, CT_PY = CT_TY + 2;
 constexpr unsigned CT_BYTES = CT_PX * CT_PY * sizeof(float);
 constexpr int CT_STRIDE = (int)(((CT_BYTES + 127) / 128) * 128 / sizeof(float));
@@ -330,19 +330,25 @@ __device__ __forceinline__ double cheb_tma_step(const Geom& g, const ChebDev& ch
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int TXn = (g.nx + CT_TX - 1) / CT_TX, TYn = (g.ny + CT_TY - 1) / CT_TY;
-  const int TZn = (g.nz + CT_ZC - 1) / CT_ZC;
-  const long long nbricks = (long long)TXn * TYn * TZn;
   const long long plane = (long long)g.nx * g.ny;
   const float c0 = ch.c0, rx = ch.rx, ry = ch.ry, rz = ch.rz;
   const int c = (ty + 1) * CT_PX + 4 + 4 * tx;  // this thread's first point in a stage
   double acc = 0.0;
+  // Bricks of TXn x TYn column tiles and TZn z ranges, dealt round-robin in
+  // x-fastest order (the blocks of a round stream whole planes together and share
+  // their halos in L2).  TZn is chosen so that the bricks fill whole rounds of the
+  // group: 16-plane bricks left a partial last round (1024 bricks at 256^3 over 608
+  // blocks kept 84% of them busy); 19 z ranges of 13-14 planes make two full rounds.
+  const long long cols = (long long)TXn * TYn;
+  const long long base = cols * ((g.nz + 15) / 16);
+  const long long rounds = (base + nblk - 1) / nblk;
+  const int TZn = (int)max(1LL, min((long long)g.nz, rounds * nblk / cols));
+  const long long nbricks = cols * TZn;
   for (long long t = blk; t < nbricks && !tm.dead; t += nblk) {
-    const int xt = (int)(t % TXn);
-    const long long u = t / TXn;
-    const int yt = (int)(u % TYn);
-    const int zt = (int)(u / TYn);
-    const int x0 = xt * CT_TX, y0 = yt * CT_TY, z0 = zt * CT_ZC;
-    const int z1 = min(z0 + CT_ZC, g.nz);
+    const long long tile = t % cols;
+    const int zt = (int)(t / cols);
+    const int x0 = (int)(tile % TXn) * CT_TX, y0 = (int)(tile / TXn) * CT_TY;
+    const int z0 = (int)((long long)zt * g.nz / TZn), z1 = (int)((long long)(zt + 1) * g.nz / TZn);
     const int nload = z1 - z0 + 2;   // planes z0-1 .. z1; load index L = plane - (z0 - 1)
     const unsigned gl = tm.gl;
     auto issue = [&](int L) {
@@ -917,12 +923,12 @@ __device__ __forceinline__ void cg_epilogue(const CgDev& a, const double* __rest
 template <int MINB, int ALG>
 __global__ void __launch_bounds__(CG_THREADS, MINB) cg_kernel(CgDev a) {
   const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (a.mode == CG_CORRECT && t0 == 0) *a.delta = 0ull;
+  if (a.mode == CG_CORRECT && t0 == 0) *a.delta = 0ull;   // the correction kernel follows
   int it;
   if constexpr (ALG == CG_CHEB) {
     it = pcg_core(a, gridDim.x, blockIdx.x);
     // vectorised path: x is x0 until the first solution update
-    cg_epilogue(a, a.ch.vec && it <= 0 ? a.x0 : a.ws.x);
+    if (a.mode != CG_CORRECT) cg_epilogue(a, a.ch.vec && it <= 0 ? a.x0 : a.ws.x);
   } else {
     if constexpr (ALG == CG_SINGLE)
       it = cg1_core(a.g, a.k, a.var != 0, a.gv, a.b, a.x0, a.rtol, a.maxit, a.ws, GridBarrier{},
@@ -930,9 +936,19 @@ __global__ void __launch_bounds__(CG_THREADS, MINB) cg_kernel(CgDev a) {
     else
       it = cg_core(a.g, a.k, a.var != 0, a.gv, a.b, a.x0, a.rtol, a.maxit, a.ws, GridBarrier{},
                    gridDim.x, blockIdx.x);
-    cg_epilogue(a, a.ws.x);
+    if (a.mode != CG_CORRECT) cg_epilogue(a, a.ws.x);
   }
   if (t0 == 0) *a.iters = it;
+}
+
+// The fused correction of Algorithm 1 after a coarse solve, as a kernel of its own
+// on the solve's stream: inside the cooperative solve kernel, whose registers the
+// iteration's passes size, the pass ran measurably slower (spilled state).  The
+// solve's iteration count tells where its solution is (x0 when the vectorised
+// preconditioned CG stopped before its first update).
+__global__ void __launch_bounds__(256) cg_correct_kernel(CgDev a) {
+  const int it = *a.iters;
+  cg_epilogue(a, a.ch.vec && it <= 0 ? a.x0 : a.ws.x);
 }
 
 __global__ void correct_kernel(const double* __restrict__ wn, const double* __restrict__ v,
@@ -1061,8 +1077,17 @@ cudaError_t cg_solve(pr_ctx* c, const CgArgs& in) {
   if (blocks > c->cg_blocks) blocks = c->cg_blocks;  // partials are sized for cg_blocks
   if (blocks < 1) blocks = 1;
   void* args[] = {&a};
+  if (a.mode == CG_CORRECT) {
+    const cudaError_t e =
+        cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(CG_THREADS), args, dsmem, c->stream);
+    if (e != cudaSuccess) return e;
+    cg_correct_kernel<<<c->num_sms * 8, 256, 0, c->stream>>>(a);
+    return cudaGetLastError();
+  }
   return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(CG_THREADS), args, dsmem, c->stream);
 }
+
+int cg_solve_launches(int mode) { return mode == CG_CORRECT ? 2 : 1; }
 
 namespace {
 

@@ -212,6 +212,9 @@ cudaError_t tri_solve_steps(pr_ctx* c, const TriTables* t, const double* in, dou
 // ---- CG coarse solver (cg.cu)
 // Epilogue modes of the cooperative CG kernel.
 enum CgMode { CG_PLAIN = 0, CG_PREDICTOR = 1, CG_CORRECT = 2 };
+// Launches of one coarse solve in the given mode (the correction runs as a kernel
+// of its own after the cooperative solve).
+int cg_solve_launches(int mode);
 struct CgArgs {
   const double* b;     // right-hand side
   const double* x0;    // start (may equal out for in-place warm start)

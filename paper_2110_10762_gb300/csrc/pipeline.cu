@@ -216,7 +216,7 @@ int run_sync_pipelined(pr_ctx* c, double* lam, pr_stats* st) {
           a.iters = c->cg_iters_dev + i;
           a.mode = CG_CORRECT;
           e = cg_solve(c, a);
-          S.launches += 1;
+          S.launches += cg_solve_launches(CG_CORRECT);
         }
       } else {
         e = correct(c, wi, vi, wi, li, di);
