@@ -96,10 +96,10 @@ NCU_TRAFFIC_PER_LUP = {"heat2d_explicit": 1016.3e6 / (63 * 1048576),
                        "heat3d_mixed": 520.4e6 / (2 * 4 * 256 ** 3)}
 # The coarse CG kernel's DRAM bytes over its algorithmic bytes (pcg_pass_costs), from
 # one ncu capture of every cg_kernel launch of a small run of the same workload
-# (profiles/pcg_cg_kernel_heat3d_256cubed_N4.md: 352.66 GB for 350.31 GB algorithmic,
-# 10 solves and 78 iterations at 256^3); traffic per launch = ratio x the bench's
-# algorithmic bytes per launch.
-NCU_COARSE_TRAFFIC_RATIO = {"heat3d_mixed": 352.66 / 350.31}
+# (profiles/pcg_cg_kernel_heat3d_256cubed_N4.md: 353.37 GB for 350.31 GB algorithmic,
+# 10 solves and 78 iterations at 256^3, the solve kernels with their correction
+# kernels); traffic per launch = ratio x the bench's algorithmic bytes per launch.
+NCU_COARSE_TRAFFIC_RATIO = {"heat3d_mixed": 353.37 / 350.31}
 
 
 def cost_model_sync(p, st, ms_per_solve):
