@@ -92,3 +92,31 @@ def test_oracle_time_to_tol_extrapolation_counts_the_work():
     # k = 2: ceil(10/4) + ceil(9/4) = 3 + 3 rounds of 4 steps at 0.5 s, plus 7 CG x 2 s
     t = bench.oracle_time_to_tol_s(p, 0.5, 2.0, 4, 2, 7)
     assert abs(t - (6 * 4 * 0.5 + 14.0)) < 1e-12
+
+
+def test_pcg_pass_costs_add_up():
+    """The per-point bytes of the preconditioned CG's passes: 16 m + 68 per iteration
+    (m - 1 Chebyshev passes, the direction pass and the solution/residual pass) and 60
+    per solve; the FP64 instruction count per iteration is the direction pass's
+    operator (6 in 3D, 4 in 2D) plus 3, the residual pass's 3 and the last
+    Chebyshev step's r.z."""
+    for dim, op in ((3, 6), (2, 4)):
+        for m in (4, 12, 16):
+            it, solve, first_dir = bench.pcg_pass_costs(dim, m)
+            assert len(it) == m + 1                       # m - 1 Chebyshev + 2 CG passes
+            assert sum(b for b, _ in it) == 16 * m + 68
+            assert sum(b for b, _ in solve) + first_dir[0] - it[-2][0] == 60
+            assert sum(f for _, f in it) == op + 3 + 3 + 1
+
+
+def test_pcg_roofline_bound_is_the_sum_of_pass_maxima():
+    """With an FP64 peak so high that no pass is FP64-bound, the bound is the HBM
+    time of the algorithmic bytes; with a low one the direction pass dominates."""
+    M, m, its, solves = 1000, 12, 7, 3
+    r = bench.pcg_roofline(M, 3, m, its, solves, 1.0, 1000.0, "measured", 1e9)
+    gbytes = M * (its * (16 * m + 68) + solves * 60)
+    assert abs(r["t_bound_ms"] - gbytes / 1000e9 * 1e3) < 1e-12
+    assert abs(r["achieved"] - gbytes / 1e-3 / 1e9) < 1e-6
+    slow = bench.pcg_roofline(M, 3, m, its, solves, 1.0, 1000.0, "measured", 1e-3)
+    assert slow["t_bound_ms"] > r["t_bound_ms"]
+    assert abs(slow["frac_of_pass_roofline"] - slow["t_bound_ms"] / 1.0) < 1e-12
