@@ -7,10 +7,12 @@
 // grid barrier and a fixed-order sum of the block partials (deterministic:
 // every block computes bit-identical scalars, so all take the same branch).
 //
-// The correction of Algorithm 1 (§4.1) is fused into the epilogue: while the
-// solution x is still in the workspace the kernel forms
+// The correction of Algorithm 1 (§4.1) follows each sweep solve in one pass
+// (cg_correct_kernel, launched right after the solve on its stream): from the
+// solution x still in the workspace it forms
 //     lam_i^{k+1} = (x + v_i) - w_i^k        (this operation order, no FMA)
-// its max-norm increment against lam_i^k (Eq. (22)), and stores w_i = x.
+// its max-norm increment against lam_i^k (Eq. (22)), and stores w_i = x.  The
+// plain and predictor stores run as the solve kernel's epilogue.
 #include <math.h>
 #include <string.h>
 
