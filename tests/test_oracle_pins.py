@@ -369,6 +369,33 @@ def test_chebyshev_preconditioner_on_a_mode(m):
     np.testing.assert_allclose(heat.chebyshev_apply(op, u, m, a, b), fac * u, rtol=1e-11, atol=1e-14)
 
 
+@pytest.mark.parametrize("m", [2, 3, 4, 12])
+def test_three_term_chebyshev_form_equals_the_oracles(m):
+    """The three-term form the vectorised GPU steps run,
+        y_{k+1} = y_k + c1_k (y_k - y_{k-1}) + c2_k (f - B y_k),  y_0 = 0, y_1 = f / c,
+    with c1_k = rho_k rho_{k-1} and c2_k = 2 rho_k / e, is the oracle's two-term
+    Chebyshev iteration (the same polynomial p_m(B) f), here in FP64 on a random right-hand
+    side of a 3D coarse operator; its first two steps use y_1 = f / c and y_0 = 0 only,
+    which is what lets the GPU form y_1 from f instead of storing it."""
+    n = (6, 5, 4)
+    h = tuple(1.0 / (k + 1) for k in n)
+    dT = 9.6 * min(h) ** 2
+    op = lambda v: v + dT * heat.apply_A(v, h, None)
+    a, b = heat.coarse_spectrum_bounds(n, h, dT)
+    c, e = 0.5 * (a + b), 0.5 * (b - a)
+    f = np.random.default_rng(210).standard_normal(tuple(reversed(n)))
+    sigma = c / e
+    rho = 1.0 / sigma
+    y_prev, y = np.zeros_like(f), f / c
+    for _ in range(1, m):
+        rho_n = 1.0 / (2.0 * sigma - rho)
+        c1, c2 = rho_n * rho, 2.0 * rho_n / e
+        y_prev, y = y, y + c1 * (y - y_prev) + c2 * (f - op(y))
+        rho = rho_n
+    ref = heat.chebyshev_apply(op, f, m, a, b)
+    np.testing.assert_allclose(y, ref, rtol=1e-12, atol=1e-13 * np.abs(ref).max())
+
+
 @pytest.mark.parametrize("var", [False, True])
 def test_coarse_spectrum_bounds(var):
     """Constant kappa: the bounds are the extreme eigenvalues; variable kappa: they
